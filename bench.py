@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point Runge-Kutta steps per second of the Taylor-Couette
+DNS step on GB300, through the libtc C ABI.
+
+Default workload: tc-257x512x512 (radius ratio 0.883, Re_i = 3000, Nr = 257,
+Ntheta = Nz = 512 Fourier modes, 768 x 768 dealiased planes), float64,
+seeded k^-2 perturbation on circular Couette flow.  One step = 3 RK substeps
+over the whole state (about 24 GB on the device, far larger than L2, so no L2
+flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference      # the CPU oracle on a bounded sample
+
+Under torchrun each rank runs an independent replica (the method does not
+shard across GPUs here: "replicas only"); value = all ranks' grid-point
+steps / max over ranks of the timed region.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK-steps/s"
+UNIT = "gridpoint-steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--workload", default="tc-257x512x512")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--sample-planes", type=int, default=4)
+    p.add_argument("--sample-pairs", type=int, default=1024)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, world, rank, backend):
+        self.world, self.rank = world, rank
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch (the roofline numerators)
+def algorithmic(w, prec):
+    """FLOPs (5 M log2 M per complex FFT of length M) and bytes per launch of
+    each kernel, per the counts written in the design notes."""
+    import math
+    Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
+    Nh, Mt, Mz = Nt // 2, 3 * Nt // 2, 3 * Nz // 2
+    f = lambda M: 5.0 * M * math.log2(M)
+    cb = 8 if prec == "mixed" else 16           # bytes of one complex intermediate
+    P = Nr * Nz * Nh
+    return {
+        "z_inverse": {"flops": 3 * Nr * Nh * f(Mz), "bytes": 3 * P * 16 + 3 * Nr * Mz * Nh * cb},
+        "theta_rows_products": {"flops": Nr * Mz * (5 * f(Mt) + 9 * Mt),
+                                "bytes": 3 * Nr * Mz * Nh * cb + 6 * Nr * Mz * Nh * cb},
+        "z_forward": {"flops": 6 * Nr * Nh * f(Mz), "bytes": 6 * Nr * Mz * Nh * cb + 6 * P * cb},
+        # line: products, u, v, w, H (read+write), new v, eta, u, w, LU and L tables
+        "line": {"flops": None, "bytes": P * (6 * cb + 48 + 64 + 64 + 120)},
+        "mean": {"flops": None, "bytes": Nr * 8 * 12},
+    }
+
+
+# ---------------------------------------------------------------------------
+def cpu_sample(args):
+    """Time the oracle (as it stands) on a bounded sample of the workload and
+    extrapolate to grid-point steps per second.  Sample: the plane phase
+    (products with the 3/2 rule) on `sample_planes` radial planes and the
+    line phase (reconstruction, explicit rows, right sides, banded solves) on
+    `sample_pairs` Fourier pairs, each for one substep; one step costs
+    3 (Nr t_plane + npairs t_pair)."""
+    import numpy as np
+    from oracle.grid import Case
+    from oracle.rk import OracleSolver
+    from oracle.fourier import products
+    from paper_0711_1429_gb300.synthetic import WORKLOADS, initial_perturbation, box_defaults
+    w = WORKLOADS[args.workload]
+    cs = Case(w["Nr"], w["Ntheta"], w["Nz"], w["zeta"], w["Re_i"], w["Re_o"], w["dt"])
+    m0, a0, rc = box_defaults(w["zeta"])
+    v, e = initial_perturbation(w["Nr"], w["Ntheta"], w["Nz"], w["seed"], w["spectrum"], w["amp"],
+                                m0=m0, alpha0=a0, rc=rc)
+    rng = np.random.default_rng(0)
+    K = min(args.sample_planes, cs.Nr)
+    sl = slice(cs.Nr // 2, cs.Nr // 2 + K)
+    t0 = time.perf_counter()
+    products(cs, v[sl], v[sl], e[sl])
+    t_plane = (time.perf_counter() - t0) / K
+    mask = np.zeros((cs.Nz, cs.Nh), dtype=bool)
+    idx = rng.choice(cs.Nz * cs.Nh, size=min(args.sample_pairs, cs.Nz * cs.Nh), replace=False)
+    mask.flat[idx] = True
+    s = OracleSolver(cs, pairs=mask)
+    s.set_fields(v=v * mask, eta=e * mask)
+    npairs = len(s.act[0])
+    P = {k: np.zeros_like(v) for k in ("uu", "uv", "uw", "vv", "vw", "ww")}
+    t0 = time.perf_counter()
+    s.advance(0, s.explicit_terms(P))
+    t_pair = (time.perf_counter() - t0) / npairs
+    total_pairs = int(cs.active_mask().sum())
+    t_step = 3.0 * (cs.Nr * t_plane + total_pairs * t_pair)
+    return {"value": cs.gridpoints / t_step, "t_step_s": t_step, "t_plane_s": t_plane,
+            "t_pair_s": t_pair, "planes": K, "pairs": npairs,
+            "sample": f"oracle plane phase on {K} of {cs.Nr} radial planes and line phase on {npairs} "
+                      f"of {total_pairs} Fourier pairs, one substep each, extrapolated to a full "
+                      f"3-substep step of {args.workload}"}
+
+
+def run_cpu_sample_subprocess(args, threads=1):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
+           "--sample-planes", str(args.sample_planes), "--sample-pairs", str(args.sample_pairs)]
+    p = subprocess.run(cmd, capture_output=True, text=True, env=env)
+    if p.returncode != 0:
+        raise RuntimeError(p.stderr[-2000:])
+    res = json.loads(p.stdout.strip().splitlines()[-1])
+    res["cores"] = threads
+    return res
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_0711_1429_gb300.synthetic import WORKLOADS
+    w = WORKLOADS[args.workload]
+    vals = []
+    t_all = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        r = run_cpu_sample_subprocess(args)
+        if i >= args.warmup:
+            vals.append(r)
+    wall = time.perf_counter() - t_all
+    t_step = statistics.mean(x["t_step_s"] for x in vals)
+    value = (w["Nr"] * w["Ntheta"] * w["Nz"]) / t_step
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import paper_0711_1429_gb300 as tc
+    from paper_0711_1429_gb300.synthetic import WORKLOADS, initial_perturbation, box_defaults
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist(world, rank, "nccl")
+    if not os.path.exists(tc.LIB_PATH):
+        from paper_0711_1429_gb300 import build as b
+        b.build()
+    w = WORKLOADS[args.workload]
+    prec = tc.TC_PREC_MIXED if args.precision == "mixed" else tc.TC_PREC_FP64
+    Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
+    gp = Nr * Nt * Nz
+    m0, a0, rc = box_defaults(w["zeta"])
+    v, e = initial_perturbation(Nr, Nt, Nz, w["seed"] + rank, w["spectrum"], w["amp"], m0=m0, alpha0=a0, rc=rc)
+    h = tc.tc_create_ex(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], precision=prec, device=local)
+    stream = torch.cuda.current_stream()
+    tc.tc_set_stream(h, stream.cuda_stream)
+    tc.tc_set_field(h, tc.TC_FIELD_V, v)
+    tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
+    peaks = tc.tc_fma_peak(local)
+    tc.tc_step(h, max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device time by CUDA events on the launch stream
+    clocks = ClockSampler(local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        tc.tc_step(h, 1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    total_ms = dist.max(total_ms)
+    value = gp * args.steps * world / (total_ms / 1e3)
+    qs = sorted(per)
+    p50 = statistics.median(qs)
+    p99 = qs[min(len(qs) - 1, int(round(0.99 * (len(qs) - 1))))]
+
+    # ---- per-kernel durations (events between kernels, unrolled steps)
+    ph = tc.tc_phase_times(h, 1)
+    alg = algorithmic(w, args.precision)
+    dom = max(ph, key=ph.get)
+    meas_peaks = {}
+    try:
+        meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = meas_peaks.get("hbm_gbs")
+    a = alg[dom]
+    t = ph[dom] * 1e-3
+    if a["flops"] is not None:
+        pk = peaks["fp32_tflops"] if args.precision == "mixed" else peaks["fp64_tflops"]
+        roof = {"bound": "alu", "achieved": a["flops"] / t / 1e12, "peak": pk, "unit": "TFLOP/s",
+                "frac": a["flops"] / t / 1e12 / pk, "traffic": None,
+                "kernel": dom, "peak_source": "measured FMA probe (tc_fma_peak) in this run",
+                "hbm_gbs_of_kernel": a["bytes"] / t / 1e9}
+    else:
+        roof = {"bound": "hbm", "achieved": a["bytes"] / t / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": (a["bytes"] / t / 1e9 / hbm) if hbm else None, "traffic": None,
+                "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)"}
+    roof["phase_ms"] = ph
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        nb = tc.tc_field_bytes(h, tc.TC_FIELD_V)
+        pin = {k: torch.empty(nb // 8, dtype=torch.float64, pin_memory=True) for k in ("vi", "ei", "vo", "eo")}
+        pin["vi"].numpy().view(np.complex128)[:] = v.ravel()
+        pin["ei"].numpy().view(np.complex128)[:] = e.ravel()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            tc.tc_set_field_ptr(h, tc.TC_FIELD_V, pin["vi"].data_ptr(), nb)
+            tc.tc_set_field_ptr(h, tc.TC_FIELD_ETA, pin["ei"].data_ptr(), nb)
+            tc.tc_step(h, 1)
+            tc.tc_get_field_ptr(h, tc.TC_FIELD_V, tc.TC_SPECTRAL, pin["vo"].data_ptr(), nb)
+            tc.tc_get_field_ptr(h, tc.TC_FIELD_ETA, tc.TC_SPECTRAL, pin["eo"].data_ptr(), nb)
+            stats = tc.tc_torque_stats(h)
+        wall = dist.max(time.perf_counter() - t0)
+        e2e = {"value": gp * args.e2e_steps * world / wall, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + 7 * 8,
+               "steps": args.e2e_steps, "torque_inner": stats["G_inner"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = run_cpu_sample_subprocess(args)
+            cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                   "sample": cpu["sample"]}
+        except Exception as ex:        # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[-300:]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "Nr": Nr, "Ntheta": Nt, "Nz": Nz,
+                       "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
+                       "precision": args.precision, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (state ~24 GB)",
+                       "device_bytes": tc.tc_device_bytes(h)},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "gpu_launches": 15 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "alu_peaks_tflops": peaks}
+    tc.tc_destroy(h)
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * tc.h -- C ABI of libtc: one GPU (sm_103a) implementation of the time step
+ * of the v-eta DNS method for Taylor-Couette flow of Pirro & Quadrio,
+ * "Direct Numerical Simulation of turbulent Taylor-Couette flow".
+ *
+ * Physical problem (Sec. 2): fluid between coaxial cylinders of radii R_i and
+ * R_o, radius ratio zeta = R_i/R_o, gap R_o - R_i = 2h.  Lengths are in h,
+ * velocities in W_i (inner-wall speed), time in h/W_i.  Re = W_i 2h / nu, so
+ * the viscous coefficient of the non-dimensional equations is 2/Re.
+ *
+ * Unknowns (Appendix): per Fourier pair (m, alpha), the radial velocity v and
+ * the radial vorticity eta as functions of r, plus the mean profiles U(r)
+ * (axial) and W(r) (azimuthal).  One call of tc_step advances them by the
+ * 3-substep implicit/explicit Runge-Kutta scheme (Sec. 2.1), each substep
+ * being: rebuild u, w from continuity, pseudo-spectral products with the 3/2
+ * rule, the radial rows of Eqs. 6 and 7 with 5-point compact explicit
+ * finite differences, and one banded radial solve per pair and variable.
+ *
+ * Conventions shared by every call:
+ *  - Spectral arrays are complex128 (re, im interleaved), shaped
+ *    [Nr][Nz][Ntheta/2], the last index fastest.  Azimuthal index j = 0 ..
+ *    Ntheta/2-1 with m = j*m0; axial slots in FFT order n = 0..Nz/2-1,
+ *    [Nz/2: Nyquist, always zero], -Nz/2+1..-1 with alpha = n*alpha0.
+ *    Slot (j=0, n<0) holds the conjugate of (0, -n).  Slot (0, 0) of U and W
+ *    holds the mean profiles; of v and eta it is zero.
+ *  - Physical arrays are float64 shaped [Nr][Mz][Mt] with Mt = 3 Ntheta/2,
+ *    Mz = 3 Nz/2, points theta_p = p Theta/Mt, z_q = q Lz/Mz.
+ *  - Host buffers are owned by the caller; every call that takes one is
+ *    synchronous with respect to that buffer.  Device memory is owned by the
+ *    handle and freed by tc_destroy.
+ *  - Return codes: 0 on success, a negative TC_ERR_* value on failure;
+ *    tc_last_error() then returns a message (thread-local).
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_handle tc_handle;
+
+enum {
+    TC_OK = 0,
+    TC_ERR_ARG = -1,        /* invalid argument */
+    TC_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    TC_ERR_NONFINITE = -3,  /* a NaN or Inf appeared in the state */
+    TC_ERR_SIZE = -4,       /* buffer size does not match the field */
+    TC_ERR_TIMEOUT = -5,    /* a bounded device wait ran out */
+    TC_ERR_STATE = -6       /* a table could not be built (zero pivot) */
+};
+
+enum {                      /* field selector of tc_get_field / tc_set_field */
+    TC_FIELD_U = 0,         /* axial velocity u (spectral: (0,0) slot = U(r)) */
+    TC_FIELD_V = 1,         /* radial velocity v */
+    TC_FIELD_W = 2,         /* azimuthal velocity w (spectral: (0,0) slot = W(r)) */
+    TC_FIELD_ETA = 3,       /* radial vorticity eta = (i m/r) u - i alpha w */
+    TC_FIELD_MEAN_U = 4,    /* mean axial profile U(r), float64 [Nr] */
+    TC_FIELD_MEAN_W = 5     /* mean azimuthal profile W(r), float64 [Nr] */
+};
+
+enum { TC_SPECTRAL = 0, TC_PHYSICAL = 1 };
+
+enum {
+    TC_PREC_FP64 = 0,       /* every step in float64 */
+    TC_PREC_MIXED = 1       /* FFTs and products in float32; radial rows,
+                               banded solves, continuity and the mean mode in
+                               float64 */
+};
+
+typedef struct {
+    int Nr, Ntheta, Nz;     /* radial points; Fourier modes in theta and z   */
+    double radius_ratio;    /* zeta = R_i/R_o, 0 < zeta < 1                    */
+    double Re_inner;        /* Re = W_i 2h/nu > 0                              */
+    double Re_outer;        /* outer-wall Reynolds number (0: outer at rest)   */
+    double dt;              /* time step in h/W_i, > 0                         */
+    double Theta;           /* azimuthal box (radians); <= 0: L_theta = 10 pi h
+                               at the centreline (Sec. 4)                      */
+    double Lz;              /* axial box in h; <= 0: 5 h (Sec. 4)              */
+    int precision;          /* TC_PREC_FP64 or TC_PREC_MIXED                  */
+    int device;             /* CUDA device ordinal; < 0: current device        */
+} tc_params;
+
+typedef struct {
+    double t;               /* time (h/W_i) */
+    long long step;         /* completed steps */
+    double G_inner;         /* torque T/(mu W_i L R_i) at the inner wall: Eq. 2
+                               read as 2 pi R_i |W' - W/r| (Table 2) */
+    double G_outer;         /* same at the outer wall: 2 pi R_o^2/R_i |W' - W/r| */
+    double Re_tau_inner;    /* u_tau h/nu with u_tau^2 = nu |W' - W/r| (Sec. 5) */
+    double Re_tau_outer;
+    double energy;          /* (1/2) <|u|^2> over the volume */
+} tc_stats;
+
+/* Create a case with the default box of Sec. 4 and float64 precision.
+ * Nr >= 9; Ntheta, Nz even, >= 4, of the form 2^a 3^b; 0 < zeta < 1; Re > 0;
+ * dt > 0.  The state starts as circular Couette flow (Eq. 1, W(R_o) =
+ * Re_outer/Re_inner) with zero perturbation.  Returns NULL on error. */
+tc_handle* tc_create(int Nr, int Ntheta, int Nz, double radius_ratio,
+                     double Re_inner, double Re_outer, double dt);
+
+/* Same with every parameter explicit. */
+tc_handle* tc_create_ex(const tc_params* params);
+
+/* Advance nsteps full Runge-Kutta steps (3 substeps each, Sec. 2.1).
+ * Launches on the handle's stream and waits for it.  Returns TC_ERR_NONFINITE
+ * if a NaN or Inf appeared in v or eta. */
+int tc_step(tc_handle* h, int nsteps);
+
+/* Advance nsub Runge-Kutta substeps (a step is 3 substeps; Sec. 2.1), without
+ * the captured graph.  Time and the step counter advance when a step is
+ * completed.  tc_step may only be called at a step boundary (it returns
+ * TC_ERR_ARG otherwise). */
+int tc_advance_substeps(tc_handle* h, int nsub);
+
+/* Copy one field into host_buf.  bytes must equal tc_field_bytes(h, which,
+ * space).  Spectral: complex128 [Nr][Nz][Ntheta/2]; physical: float64
+ * [Nr][Mz][Mt]; MEAN_U/MEAN_W: float64 [Nr] (space ignored). */
+int tc_get_field(tc_handle* h, int which, int space, void* host_buf, size_t bytes);
+
+/* Replace v (TC_FIELD_V), eta (TC_FIELD_ETA) or a mean profile (MEAN_U,
+ * MEAN_W) from a host buffer (spectral layout / float64 [Nr]).  The m = 0
+ * column is made Hermitian from its n > 0 slots, the Nyquist slot and (0,0)
+ * are zeroed.  The Runge-Kutta memory restarts from this state. */
+int tc_set_field(tc_handle* h, int which, const void* host_buf, size_t bytes);
+
+/* Bytes of one field in the given space. */
+size_t tc_field_bytes(const tc_handle* h, int which, int space);
+
+/* Torque, friction Reynolds numbers and kinetic energy of the current state. */
+int tc_torque_stats(tc_handle* h, tc_stats* out);
+
+/* Launch stream (a cudaStream_t, or NULL for the legacy default stream). */
+int tc_set_stream(tc_handle* h, void* cuda_stream);
+
+/* Device bytes held by the handle. */
+size_t tc_device_bytes(const tc_handle* h);
+
+void tc_destroy(tc_handle* h);
+
+/* Measurement helpers (no counterpart in the paper). */
+
+#define TC_NPHASES 5
+/* Run nsteps steps kernel by kernel (no graph) with CUDA events between the
+ * kernels on the handle's stream; ms[i] receives the average duration of one
+ * launch of kernel i: 0 inverse z FFT, 1 theta transforms + products,
+ * 2 forward z FFT, 3 line phase (Eqs. 6-7 rows and solves), 4 mean flow.
+ * nphases must be >= TC_NPHASES.  The state advances by nsteps. */
+int tc_phase_times(tc_handle* h, int nsteps, double* ms, int nphases);
+
+/* Fused multiply-add throughput of the device (TFLOP/s, 2 flops per FMA) in
+ * float64 and float32, from a short probe kernel; device < 0: current. */
+int tc_fma_peak(int device, double* fp64_tflops, double* fp32_tflops);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* tc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

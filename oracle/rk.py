@@ -18,6 +18,7 @@ This module stores E of the previous substep explicitly (the plain form).
 """
 from fractions import Fraction
 import numpy as np
+from scipy.linalg import solve_banded
 
 from .stencils import build_stencils
 from .fourier import products
@@ -44,12 +45,16 @@ class OracleSolver:
     W = A r + B/r (Eq. 1 with W(R_i) = 1, W(R_o) = Re_o/Re_i) and zero
     perturbation."""
 
-    def __init__(self, case, stencils=None):
+    def __init__(self, case, stencils=None, pairs=None):
+        """pairs: optional boolean (Nz, Nh) mask restricting the evolved pairs
+        (the others stay zero); used to check sampled pairs of large cases."""
         self.case = case
         self.S = stencils if stencils is not None else build_stencils(case.r)
         cs = case
         self.r_col = cs.r.reshape(-1, 1)
         mask = cs.active_mask()
+        if pairs is not None:
+            mask = mask & pairs
         self.act = np.nonzero(mask)          # (n-slot, j) of active pairs
         m_full = np.broadcast_to(cs.m_of()[0], (cs.Nz, cs.Nh))
         a_full = np.broadcast_to(cs.alpha_of()[0], (cs.Nz, cs.Nh))
@@ -100,6 +105,7 @@ class OracleSolver:
         Nyquist slot and (0, 0) of v, eta are zero."""
         F[:, self.conj_dst, 0] = np.conj(F[:, self.conj_src, 0])
         F[:, self.case.Nz // 2, :] = 0.0
+        F[:, 0, 0] = 0.0
 
     def velocity(self):
         """Spectral u (axial), v (radial), w (azimuthal); (0,0) holds U, 0, W."""
@@ -113,11 +119,13 @@ class OracleSolver:
         return u, v, w
 
     # ---- one substep ----------------------------------------------------------
-    def explicit_terms(self):
-        """E(x) for v, eta (active pairs) and for U, W."""
+    def explicit_terms(self, P=None):
+        """E(x) for v, eta (active pairs) and for U, W; the products P (dict of
+        spectral arrays) are formed from the current velocity unless given."""
         cs = self.case
         u, v, w = self.velocity()
-        P = products(cs, u, v, w)
+        if P is None:
+            P = products(cs, u, v, w)
         Pa = {k: self._gather(P[k]) for k in P}
         ua, va, wa = self._gather(u), self._gather(v), self._gather(w)
         Ev = op.v_explicit(self.S, self.r_col, self.m, self.alpha, cs.nu, self.coef, ua, va, wa, Pa)
@@ -126,11 +134,14 @@ class OracleSolver:
         return {"v": Ev, "eta": Ee, "U": EU, "W": EW}
 
     def substep(self, k):
+        self.advance(k, self.explicit_terms())
+
+    def advance(self, k, E):
+        """Right sides and banded solves of substep k, given E(x^(k-1))."""
         cs = self.case
         al, be, ga, ze = SMR91.floats()
         dt = cs.dt
         Nr = cs.Nr
-        E = self.explicit_terms()
         Ep = self.E_prev if self.E_prev is not None else {key: 0.0 * val for key, val in E.items()}
         ex = lambda key: dt * (ga[k] * E[key] + ze[k] * Ep[key])
 
@@ -151,7 +162,6 @@ class OracleSolver:
         e_new = op.solve_rows(op.eta_system(self.S, A), rhs)
 
         # mean flow
-        from scipy.linalg import solve_banded
         rW = (op.band_apply(self.S, self.MW, self.W) + al[k] * dt * op.band_apply(self.S, self.LW, self.W)
               + ex("W"))
         rW[0], rW[Nr - 1] = 1.0, cs.W_outer

@@ -1,0 +1,205 @@
+"""Python binding of libtc (include/tc.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of libtc.so; this module
+converts numpy arrays to host pointers and return codes to exceptions.  It
+loads the in-tree library on first use and raises if it has not been built
+(there is no fallback path).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+HEADER = os.path.join(_HERE, "..", "include", "tc.h")
+
+TC_OK, TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_NONFINITE, TC_ERR_SIZE, TC_ERR_TIMEOUT, TC_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+TC_FIELD_U, TC_FIELD_V, TC_FIELD_W, TC_FIELD_ETA, TC_FIELD_MEAN_U, TC_FIELD_MEAN_W = range(6)
+TC_SPECTRAL, TC_PHYSICAL = 0, 1
+TC_PREC_FP64, TC_PREC_MIXED = 0, 1
+
+
+class TcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libtc error {code}: {msg}")
+        self.code = code
+
+
+class tc_params(ctypes.Structure):
+    _fields_ = [("Nr", ctypes.c_int), ("Ntheta", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("radius_ratio", ctypes.c_double), ("Re_inner", ctypes.c_double),
+                ("Re_outer", ctypes.c_double), ("dt", ctypes.c_double),
+                ("Theta", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("precision", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class tc_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_longlong),
+                ("G_inner", ctypes.c_double), ("G_outer", ctypes.c_double),
+                ("Re_tau_inner", ctypes.c_double), ("Re_tau_outer", ctypes.c_double),
+                ("energy", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libtc.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_0711_1429_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    L.tc_create.restype = vp
+    L.tc_create.argtypes = [i, i, i, d, d, d, d]
+    L.tc_create_ex.restype = vp
+    L.tc_create_ex.argtypes = [ctypes.POINTER(tc_params)]
+    L.tc_step.restype = i
+    L.tc_step.argtypes = [vp, i]
+    L.tc_advance_substeps.restype = i
+    L.tc_advance_substeps.argtypes = [vp, i]
+    L.tc_get_field.restype = i
+    L.tc_get_field.argtypes = [vp, i, i, vp, sz]
+    L.tc_set_field.restype = i
+    L.tc_set_field.argtypes = [vp, i, vp, sz]
+    L.tc_field_bytes.restype = sz
+    L.tc_field_bytes.argtypes = [vp, i, i]
+    L.tc_torque_stats.restype = i
+    L.tc_torque_stats.argtypes = [vp, ctypes.POINTER(tc_stats)]
+    L.tc_set_stream.restype = i
+    L.tc_set_stream.argtypes = [vp, vp]
+    L.tc_device_bytes.restype = sz
+    L.tc_device_bytes.argtypes = [vp]
+    L.tc_destroy.restype = None
+    L.tc_destroy.argtypes = [vp]
+    L.tc_phase_times.restype = i
+    L.tc_phase_times.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), i]
+    L.tc_fma_peak.restype = i
+    L.tc_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.tc_last_error.restype = ctypes.c_char_p
+    L.tc_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def declared_functions():
+    """Names of the functions declared in include/tc.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tc_[a-z_]+)\s*\(", src)))
+
+
+def _check(rc):
+    if rc != TC_OK:
+        raise TcError(rc, lib().tc_last_error().decode())
+    return rc
+
+
+def tc_create(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt):
+    h = lib().tc_create(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt)
+    if not h:
+        raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
+    return h
+
+
+def tc_create_ex(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0, Lz=0.0,
+                 precision=TC_PREC_FP64, device=-1):
+    p = tc_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device)
+    h = lib().tc_create_ex(ctypes.byref(p))
+    if not h:
+        raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
+    return h
+
+
+def tc_step(h, nsteps=1):
+    return _check(lib().tc_step(h, nsteps))
+
+
+def tc_advance_substeps(h, nsub=1):
+    return _check(lib().tc_advance_substeps(h, nsub))
+
+
+def tc_field_bytes(h, which, space=TC_SPECTRAL):
+    return lib().tc_field_bytes(h, which, space)
+
+
+def _field_shape(h, which, space):
+    nbytes = tc_field_bytes(h, which, space)
+    if which in (TC_FIELD_MEAN_U, TC_FIELD_MEAN_W):
+        return (nbytes // 8,), np.float64
+    if space == TC_PHYSICAL:
+        return (nbytes // 8,), np.float64
+    return (nbytes // 16,), np.complex128
+
+
+def tc_get_field(h, which, space=TC_SPECTRAL, out=None):
+    """Copy a field into `out` (a C-contiguous numpy array of the right byte
+    size) or a new flat array; reshape with the case's dimensions."""
+    if out is None:
+        shape, dt = _field_shape(h, which, space)
+        out = np.empty(shape, dtype=dt)
+    if not out.flags.c_contiguous:
+        raise ValueError("output array must be C-contiguous")
+    _check(lib().tc_get_field(h, which, space, out.ctypes.data, out.nbytes))
+    return out
+
+
+def tc_set_field(h, which, arr):
+    arr = np.ascontiguousarray(arr)
+    if which in (TC_FIELD_MEAN_U, TC_FIELD_MEAN_W):
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+    else:
+        arr = np.ascontiguousarray(arr, dtype=np.complex128)
+    return _check(lib().tc_set_field(h, which, arr.ctypes.data, arr.nbytes))
+
+
+def tc_set_field_ptr(h, which, host_ptr, nbytes):
+    """Same as tc_set_field from a raw host pointer (e.g. pinned memory)."""
+    return _check(lib().tc_set_field(h, which, host_ptr, nbytes))
+
+
+def tc_get_field_ptr(h, which, space, host_ptr, nbytes):
+    return _check(lib().tc_get_field(h, which, space, host_ptr, nbytes))
+
+
+def tc_torque_stats(h):
+    s = tc_stats()
+    _check(lib().tc_torque_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in tc_stats._fields_}
+
+
+def tc_set_stream(h, stream_ptr):
+    return _check(lib().tc_set_stream(h, stream_ptr))
+
+
+def tc_device_bytes(h):
+    return lib().tc_device_bytes(h)
+
+
+def tc_destroy(h):
+    if h:
+        lib().tc_destroy(h)
+
+
+PHASES = ("z_inverse", "theta_rows_products", "z_forward", "line", "mean")
+
+
+def tc_phase_times(h, nsteps=1):
+    """Average ms per launch of each kernel of the step (dict)."""
+    ms = (ctypes.c_double * len(PHASES))()
+    _check(lib().tc_phase_times(h, nsteps, ms, len(PHASES)))
+    return dict(zip(PHASES, list(ms)))
+
+
+def tc_fma_peak(device=-1):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tc_fma_peak(device, ctypes.byref(a), ctypes.byref(b)))
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value}
+
+
+def tc_last_error():
+    return lib().tc_last_error().decode()

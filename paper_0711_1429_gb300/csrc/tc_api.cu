@@ -1,0 +1,671 @@
+// C ABI of libtc: handle life cycle, host-side tables (radial grid, compact
+// stencils, FFT plans and twiddles, the reversed factorisation of the
+// averaging stencil), the captured Runge-Kutta step, field I/O and
+// diagnostics.  See include/tc.h for the contract of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tc_internal.h"
+#include "../../include/tc.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const std::string& s) { g_err = s; }
+
+#define CK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            set_err(std::string(#call) + ": " + cudaGetErrorString(_e));          \
+            return TC_ERR_CUDA;                                                   \
+        }                                                                         \
+    } while (0)
+
+typedef long double ld;
+
+// ---- exact-order dense solve in long double (partial pivoting) --------------
+bool solve_ld(int n, std::vector<ld>& A, std::vector<ld>& b) {
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < n; ++i)
+            if (fabsl(A[i * n + col]) > fabsl(A[piv * n + col])) piv = i;
+        if (A[piv * n + col] == 0.0L) return false;
+        if (piv != col) {
+            for (int k = 0; k < n; ++k) std::swap(A[col * n + k], A[piv * n + k]);
+            std::swap(b[col], b[piv]);
+        }
+        for (int i = col + 1; i < n; ++i) {
+            const ld f = A[i * n + col] / A[col * n + col];
+            if (f == 0.0L) continue;
+            for (int k = col; k < n; ++k) A[i * n + k] -= f * A[col * n + k];
+            b[i] -= f * b[col];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        ld s = b[i];
+        for (int k = i + 1; k < n; ++k) s -= A[i * n + k] * b[k];
+        b[i] = s / A[i * n + i];
+    }
+    return true;
+}
+
+// Scaled monomial p_q(x) = ((x - xc)/h)^q and its derivatives times h^k:
+// h^k D^k p_q = q!/(q-k)! ((x - xc)/h)^(q-k).
+ld hder(int q, int k, ld x, ld xc, ld h) {
+    if (k > q) return 0.0L;
+    ld f = 1.0L;
+    for (int t = 0; t < k; ++t) f *= (ld)(q - t);
+    return f * powl((x - xc) / h, (ld)(q - k));
+}
+// h^n times the chain operators D, D D_*, D D_* D D_* applied to p_q at x
+ld hop(int which, int q, ld x, ld xc, ld h) {
+    const ld y = h / x;   // h/r
+    switch (which) {
+        case 0: return hder(q, 0, x, xc, h);
+        case 1: return hder(q, 1, x, xc, h);
+        case 2: return hder(q, 2, x, xc, h) + y * hder(q, 1, x, xc, h) - y * y * hder(q, 0, x, xc, h);
+        default:
+            return hder(q, 4, x, xc, h) + 2 * y * hder(q, 3, x, xc, h) - 3 * y * y * hder(q, 2, x, xc, h)
+                   + 3 * y * y * y * hder(q, 1, x, xc, h) - 3 * y * y * y * y * hder(q, 0, x, xc, h);
+    }
+}
+
+struct HostStencils {
+    std::vector<int> start;
+    std::vector<double> d0, l1, l2, l4, dwall, dsol;
+};
+
+// Stencils of the 5-point compact explicit scheme (see the oracle's notes on
+// the reading): interior rows make D D_* D D_* exact to degree 8 jointly with
+// d0 (sum d0 = 1), then D D_* and D exact to degree 4 against that d0;
+// near-wall rows 1, Nr-2 explicit one-sided to degree 4; wall derivative
+// rows for the Neumann condition and the wall shear.
+bool build_stencils(const std::vector<double>& r, HostStencils& S) {
+    const int N = (int)r.size();
+    S.start.assign(N, 0);
+    S.d0.assign(N * 5, 0.0); S.l1.assign(N * 5, 0.0); S.l2.assign(N * 5, 0.0); S.l4.assign(N * 5, 0.0);
+    S.dwall.assign(10, 0.0);
+    for (int j = 2; j <= N - 3; ++j) {
+        const int st = j - 2;
+        S.start[j] = st;
+        const ld xc = r[j], h = ((ld)r[st + 4] - (ld)r[st]) / 4.0L;
+        std::vector<ld> A(100, 0.0L), b(10, 0.0L);
+        for (int q = 0; q < 9; ++q) {
+            for (int s = 0; s < 5; ++s) {
+                A[q * 10 + s] = -hop(3, q, r[st + s], xc, h);       // d0 unknowns
+                A[q * 10 + 5 + s] = hop(0, q, r[st + s], xc, h);    // h^4 l4 unknowns
+            }
+        }
+        for (int s = 0; s < 5; ++s) A[9 * 10 + s] = 1.0L;
+        b[9] = 1.0L;
+        if (!solve_ld(10, A, b)) return false;
+        ld d0[5];
+        for (int s = 0; s < 5; ++s) {
+            d0[s] = b[s];
+            S.d0[j * 5 + s] = (double)b[s];
+            S.l4[j * 5 + s] = (double)(b[5 + s] / (h * h * h * h));
+        }
+        for (int which = 1; which <= 2; ++which) {
+            std::vector<ld> M(25), rhs(5);
+            for (int q = 0; q < 5; ++q) {
+                ld acc = 0.0L;
+                for (int s = 0; s < 5; ++s) {
+                    M[q * 5 + s] = hop(0, q, r[st + s], xc, h);
+                    acc += d0[s] * hop(which, q, r[st + s], xc, h);
+                }
+                rhs[q] = acc;
+            }
+            if (!solve_ld(5, M, rhs)) return false;
+            const ld hp = which == 1 ? h : h * h;
+            for (int s = 0; s < 5; ++s) (which == 1 ? S.l1 : S.l2)[j * 5 + s] = (double)(rhs[s] / hp);
+        }
+    }
+    auto one_sided = [&](int st, ld xe, int which, double* out) -> bool {
+        const ld h = ((ld)r[st + 4] - (ld)r[st]) / 4.0L;
+        std::vector<ld> M(25), rhs(5);
+        for (int q = 0; q < 5; ++q) {
+            for (int s = 0; s < 5; ++s) M[q * 5 + s] = hop(0, q, r[st + s], xe, h);
+            rhs[q] = hop(which, q, xe, xe, h);
+        }
+        if (!solve_ld(5, M, rhs)) return false;
+        const ld hp = which == 1 ? h : h * h;
+        for (int s = 0; s < 5; ++s) out[s] = (double)(rhs[s] / hp);
+        return true;
+    };
+    const int rows[2] = {1, N - 2}, starts[2] = {0, N - 5};
+    for (int t = 0; t < 2; ++t) {
+        const int j = rows[t], st = starts[t];
+        S.start[j] = st;
+        S.d0[j * 5 + (j - st)] = 1.0;
+        if (!one_sided(st, r[j], 1, &S.l1[j * 5])) return false;
+        if (!one_sided(st, r[j], 2, &S.l2[j * 5])) return false;
+    }
+    S.start[N - 1] = N - 5;
+    if (!one_sided(0, r[0], 1, &S.dwall[0])) return false;
+    if (!one_sided(N - 5, r[N - 1], 1, &S.dwall[5])) return false;
+
+    // Factorisation of the d0 rows 2..N-3 on the unknowns Dv_2..Dv_{N-3},
+    // eliminated from the outer wall inwards (row order N-3, N-4, ..., 2):
+    // per row (m2, m1, 1/diag, c, e) with m2, m1 referring to rows j+2, j+1
+    // and c, e to columns j-1, j-2.
+    S.dsol.assign(N * 5, 0.0);
+    std::vector<ld> Ud(N, 1.0L), Uc(N, 0.0L), Ue(N, 0.0L);
+    for (int j = N - 3; j >= 2; --j) {
+        const double* w = &S.d0[j * 5];
+        const ld m2 = (j + 2 <= N - 3) ? w[4] / Ud[j + 2] : 0.0L;
+        const ld t3 = (j + 1 <= N - 3) ? (ld)w[3] - m2 * Uc[j + 2] : 0.0L;
+        const ld t2 = (ld)w[2] - m2 * ((j + 2 <= N - 3) ? Ue[j + 2] : 0.0L);
+        const ld m1 = (j + 1 <= N - 3) ? t3 / Ud[j + 1] : 0.0L;
+        Ud[j] = t2 - m1 * ((j + 1 <= N - 3) ? Uc[j + 1] : 0.0L);
+        Uc[j] = (j - 1 >= 2) ? (ld)w[1] - m1 * ((j + 1 <= N - 3) ? Ue[j + 1] : 0.0L) : 0.0L;
+        Ue[j] = (j - 2 >= 2) ? (ld)w[0] : 0.0L;
+        if (Ud[j] == 0.0L) return false;
+        S.dsol[j * 5 + 0] = (double)m2;
+        S.dsol[j * 5 + 1] = (double)m1;
+        S.dsol[j * 5 + 2] = (double)(1.0L / Ud[j]);
+        S.dsol[j * 5 + 3] = (double)Uc[j];
+        S.dsol[j * 5 + 4] = (double)Ue[j];
+    }
+    return true;
+}
+
+// Mixed-radix Stockham plan: radix-3 stages first, then 4, then 2.
+bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim) {
+    p.M = M;
+    p.nst = 0;
+    int m = M, Ns = 1, off = 0;
+    std::vector<int> radices;
+    while (m % 3 == 0) { radices.push_back(3); m /= 3; }
+    while (m % 4 == 0) { radices.push_back(4); m /= 4; }
+    while (m % 2 == 0) { radices.push_back(2); m /= 2; }
+    if (m != 1 || (int)radices.size() > TC_MAX_STAGES) return false;
+    const ld twopi = 6.283185307179586476925286766559005768L;
+    for (int R : radices) {
+        p.R[p.nst] = R;
+        p.Ns[p.nst] = Ns;
+        p.twoff[p.nst] = off;
+        for (int jm = 0; jm < Ns; ++jm)
+            for (int r = 1; r < R; ++r) {
+                const ld a = -twopi * (ld)(r * jm) / (ld)(Ns * R);
+                twre.push_back(cosl(a));
+                twim.push_back(sinl(a));
+            }
+        off += Ns * (R - 1);
+        Ns *= R;
+        p.nst++;
+    }
+    p.ntw = off;
+    return true;
+}
+
+bool is_2a3b(int n) {
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+}  // namespace
+
+struct tc_handle {
+    tc_params prm;
+    TcDev d;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<void*> allocs;
+    size_t dev_bytes = 0;
+    bool need_init = true;
+    int phase = 0;                 // next substep (0..2)
+    double t = 0.0;
+    long long step = 0;
+    std::vector<double> r;
+    HostStencils S;
+    double Ri = 0, Ro = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(tc_handle* h, T*& p, size_t count) {
+    void* q = nullptr;
+    const size_t bytes = count * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_err(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return TC_ERR_CUDA;
+    }
+    h->allocs.push_back(q);
+    h->dev_bytes += bytes;
+    p = static_cast<T*>(q);
+    return TC_OK;
+}
+
+template <typename T>
+int upload(tc_handle* h, const T*& dst, const std::vector<T>& src) {
+    T* p = nullptr;
+    int rc = dalloc(h, p, src.size());
+    if (rc) return rc;
+    CK(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    dst = p;
+    return TC_OK;
+}
+
+void free_all(tc_handle* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+int init_handle(tc_handle* h) {
+    const tc_params& P = h->prm;
+    TcDev& d = h->d;
+    std::memset(&d, 0, sizeof(d));
+    d.Nr = P.Nr;
+    d.Nz = P.Nz;
+    d.Nh = P.Ntheta / 2;
+    d.Mt = 3 * P.Ntheta / 2;
+    d.Mz = 3 * P.Nz / 2;
+    d.npairs = d.Nz * d.Nh;
+    d.mixed = P.precision == TC_PREC_MIXED ? 1 : 0;
+    d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
+    d.dt = P.dt;
+    d.nu = 2.0 / P.Re_inner;
+    d.W_outer = P.Re_outer / P.Re_inner;
+    // grid: R_i = 2 zeta/(1 - zeta), r_j = R_i + (2 j)/(Nr - 1)
+    const double Ri = 2.0 * P.radius_ratio / (1.0 - P.radius_ratio);
+    h->r.resize(P.Nr);
+    for (int j = 0; j < P.Nr; ++j) h->r[j] = Ri + (2.0 * (double)j) / (double)(P.Nr - 1);
+    h->Ri = Ri;
+    h->Ro = h->r[P.Nr - 1];
+    const double rc = Ri + 1.0;
+    const double Theta = P.Theta > 0 ? P.Theta : 10.0 * M_PI / rc;
+    const double Lz = P.Lz > 0 ? P.Lz : 5.0;
+    d.m0 = 2.0 * M_PI / Theta;
+    d.alpha0 = 2.0 * M_PI / Lz;
+    // Runge-Kutta (Spalart, Moser & Rogers 1991, Crank-Nicolson per substep)
+    const double ga[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+    const double ze[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+    const double ab[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
+    for (int k = 0; k < 3; ++k) {
+        d.rk_gamma[k] = ga[k]; d.rk_zeta[k] = ze[k]; d.rk_alpha[k] = ab[k]; d.rk_beta[k] = ab[k];
+    }
+    if (!build_stencils(h->r, h->S)) { set_err("stencil construction failed"); return TC_ERR_STATE; }
+    int rc_ = TC_OK;
+    std::vector<double> rinv(P.Nr);
+    for (int j = 0; j < P.Nr; ++j) rinv[j] = 1.0 / h->r[j];
+    if ((rc_ = upload(h, d.r, h->r))) return rc_;
+    if ((rc_ = upload(h, d.rinv, rinv))) return rc_;
+    if ((rc_ = upload(h, d.start, h->S.start))) return rc_;
+    if ((rc_ = upload(h, d.d0, h->S.d0))) return rc_;
+    if ((rc_ = upload(h, d.l1, h->S.l1))) return rc_;
+    if ((rc_ = upload(h, d.l2, h->S.l2))) return rc_;
+    if ((rc_ = upload(h, d.l4, h->S.l4))) return rc_;
+    if ((rc_ = upload(h, d.dwall, h->S.dwall))) return rc_;
+    if ((rc_ = upload(h, d.dsol, h->S.dsol))) return rc_;
+    // FFT plans
+    std::vector<ld> zr, zi, tr, ti;
+    if (!make_plan(d.Mz, d.pz, zr, zi) || !make_plan(d.Mt, d.pt, tr, ti)) {
+        set_err("FFT length is not of the form 2^a 3^b");
+        return TC_ERR_ARG;
+    }
+    std::vector<double2> twz_d(zr.size()), twt_d(tr.size());
+    std::vector<float2> twz_f(zr.size()), twt_f(tr.size());
+    for (size_t i = 0; i < zr.size(); ++i) { twz_d[i] = make_double2((double)zr[i], (double)zi[i]); twz_f[i] = make_float2((float)zr[i], (float)zi[i]); }
+    for (size_t i = 0; i < tr.size(); ++i) { twt_d[i] = make_double2((double)tr[i], (double)ti[i]); twt_f[i] = make_float2((float)tr[i], (float)ti[i]); }
+    if (twz_d.empty()) { twz_d.push_back(make_double2(1, 0)); twz_f.push_back(make_float2(1, 0)); }
+    if (twt_d.empty()) { twt_d.push_back(make_double2(1, 0)); twt_f.push_back(make_float2(1, 0)); }
+    if ((rc_ = upload(h, d.twz_d, twz_d))) return rc_;
+    if ((rc_ = upload(h, d.twt_d, twt_d))) return rc_;
+    if ((rc_ = upload(h, d.twz_f, twz_f))) return rc_;
+    if ((rc_ = upload(h, d.twt_f, twt_f))) return rc_;
+    // fields
+    const size_t P1 = (size_t)d.Nr * d.npairs;
+    double2* f[6];
+    for (int i = 0; i < 6; ++i) if ((rc_ = dalloc(h, f[i], P1))) return rc_;
+    d.v = f[0]; d.eta = f[1]; d.u = f[2]; d.w = f[3]; d.Hv = f[4]; d.He = f[5];
+    for (int i = 0; i < 6; ++i) CK(cudaMemset(f[i], 0, P1 * sizeof(double2)));
+    double2* pr;
+    if ((rc_ = dalloc(h, pr, 6 * P1))) return rc_;
+    CK(cudaMemset(pr, 0, 6 * P1 * sizeof(double2)));
+    d.prod = pr;
+    const size_t Z1 = (size_t)d.Nr * d.Mz * d.Nh;
+    double2 *zb, *pb;
+    if ((rc_ = dalloc(h, zb, 3 * Z1))) return rc_;
+    if ((rc_ = dalloc(h, pb, 6 * Z1))) return rc_;
+    d.zbuf = zb; d.pbuf = pb;
+    double* mean;
+    if ((rc_ = dalloc(h, mean, 5 * (size_t)d.Nr))) return rc_;
+    d.U = mean; d.W = mean + d.Nr; d.HU = mean + 2 * d.Nr; d.HW = mean + 3 * d.Nr; d.eprof = mean + 4 * d.Nr;
+    CK(cudaMemset(mean, 0, 5 * (size_t)d.Nr * sizeof(double)));
+    // circular Couette flow W = A r + B/r, W(R_i) = 1, W(R_o) = Re_o/Re_i
+    {
+        const double Ro = h->Ro, Wo = d.W_outer;
+        const double A = (Wo * Ro - Ri) / (Ro * Ro - Ri * Ri);
+        const double B = Ri - A * Ri * Ri;
+        std::vector<double> W(P.Nr);
+        for (int j = 0; j < P.Nr; ++j) W[j] = A * h->r[j] + B / h->r[j];
+        CK(cudaMemcpy(d.W, W.data(), P.Nr * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // per-pair tables
+    if ((rc_ = dalloc(h, d.tab_luv, 3 * (size_t)d.Nr * 5 * d.npairs))) return rc_;
+    if ((rc_ = dalloc(h, d.tab_lue, 3 * (size_t)d.Nr * 5 * d.npairs))) return rc_;
+    if ((rc_ = dalloc(h, d.tab_lv, (size_t)d.Nr * 5 * d.npairs))) return rc_;
+    int* flag;
+    if ((rc_ = dalloc(h, flag, 4))) return rc_;
+    CK(cudaMemset(flag, 0, 4 * sizeof(int)));
+    d.flag = flag;
+    CK(tc_set_kernel_attributes());
+    CK(tc_set_line_kernel_attributes());
+    tc_launch_setup_tables(d, h->stream);
+    CK(cudaGetLastError());
+    int hf[4];
+    CK(cudaMemcpy(hf, d.flag, sizeof(hf), cudaMemcpyDeviceToHost));
+    if (hf[1]) { set_err("a radial system has a vanishing pivot (LU without pivoting)"); return TC_ERR_STATE; }
+    h->need_init = true;
+    return TC_OK;
+}
+
+int ensure_init(tc_handle* h) {
+    if (!h->need_init) return TC_OK;
+    tc_launch_init_state(h->d, h->stream);
+    CK(cudaGetLastError());
+    h->need_init = false;
+    return TC_OK;
+}
+
+void launch_step(tc_handle* h, cudaStream_t s) {
+    for (int k = 0; k < 3; ++k) {
+        tc_launch_plane_phase(h->d, s);
+        tc_launch_line_phase(h->d, k, s);
+        tc_launch_mean_phase(h->d, k, s);
+    }
+}
+
+int ensure_graph(tc_handle* h) {
+    if (h->graph) return TC_OK;
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    launch_step(h, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); set_err(std::string("graph capture: ") + cudaGetErrorString(e)); return TC_ERR_CUDA; }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { set_err(std::string("graph instantiate: ") + cudaGetErrorString(e)); return TC_ERR_CUDA; }
+    return TC_OK;
+}
+
+int validate(const tc_params* p) {
+    if (!p) { set_err("null parameters"); return TC_ERR_ARG; }
+    if (p->Nr < 9) { set_err("Nr must be >= 9"); return TC_ERR_ARG; }
+    if (p->Ntheta < 4 || p->Ntheta % 2 || !is_2a3b(p->Ntheta)) { set_err("Ntheta must be even, >= 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
+    if (p->Nz < 4 || p->Nz % 2 || !is_2a3b(p->Nz)) { set_err("Nz must be even, >= 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
+    if (!(p->radius_ratio > 0.0 && p->radius_ratio < 1.0)) { set_err("radius ratio must lie in (0, 1)"); return TC_ERR_ARG; }
+    if (!(p->Re_inner > 0.0) || !std::isfinite(p->Re_outer)) { set_err("Re_inner must be > 0 and Re_outer finite"); return TC_ERR_ARG; }
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { set_err("dt must be > 0"); return TC_ERR_ARG; }
+    if (p->precision != TC_PREC_FP64 && p->precision != TC_PREC_MIXED) { set_err("unknown precision"); return TC_ERR_ARG; }
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tc_last_error(void) { return g_err.c_str(); }
+
+tc_handle* tc_create_ex(const tc_params* params) {
+    if (validate(params)) return nullptr;
+    if (params->device >= 0) {
+        cudaError_t e = cudaSetDevice(params->device);
+        if (e != cudaSuccess) { set_err(std::string("cudaSetDevice: ") + cudaGetErrorString(e)); return nullptr; }
+    }
+    tc_handle* h = new tc_handle();
+    h->prm = *params;
+    int rc = init_handle(h);
+    if (rc) {
+        std::string msg = g_err;
+        free_all(h);
+        delete h;
+        set_err(msg);
+        return nullptr;
+    }
+    g_err.clear();
+    return h;
+}
+
+tc_handle* tc_create(int Nr, int Ntheta, int Nz, double radius_ratio, double Re_inner,
+                     double Re_outer, double dt) {
+    tc_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.Nr = Nr; p.Ntheta = Ntheta; p.Nz = Nz; p.radius_ratio = radius_ratio;
+    p.Re_inner = Re_inner; p.Re_outer = Re_outer; p.dt = dt;
+    p.Theta = 0.0; p.Lz = 0.0; p.precision = TC_PREC_FP64; p.device = -1;
+    return tc_create_ex(&p);
+}
+
+void tc_destroy(tc_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int tc_set_stream(tc_handle* h, void* s) {
+    if (!h) { set_err("null handle"); return TC_ERR_ARG; }
+    h->stream = (cudaStream_t)s;
+    return TC_OK;
+}
+
+static int check_flags(tc_handle* h) {
+    int hf[4];
+    CK(cudaMemcpy(hf, h->d.flag, sizeof(hf), cudaMemcpyDeviceToHost));
+    if (hf[0]) { set_err("non-finite value in v or eta"); return TC_ERR_NONFINITE; }
+    return TC_OK;
+}
+
+int tc_advance_substeps(tc_handle* h, int nsub) {
+    if (!h || nsub < 0) { set_err("invalid handle or substep count"); return TC_ERR_ARG; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    for (int n = 0; n < nsub; ++n) {
+        const int k = h->phase;
+        tc_launch_plane_phase(h->d, h->stream);
+        tc_launch_line_phase(h->d, k, h->stream);
+        tc_launch_mean_phase(h->d, k, h->stream);
+        CK(cudaGetLastError());
+        h->phase = (k + 1) % 3;
+        if (h->phase == 0) { h->t += h->d.dt; h->step += 1; }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return check_flags(h);
+}
+
+int tc_step(tc_handle* h, int nsteps) {
+    if (!h || nsteps < 0) { set_err("invalid handle or step count"); return TC_ERR_ARG; }
+    if (h->phase != 0) { set_err("tc_step called inside a step; finish it with tc_advance_substeps"); return TC_ERR_ARG; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    if ((rc = ensure_graph(h))) return rc;
+    for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->graph, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->t += nsteps * h->d.dt;
+    h->step += nsteps;
+    return check_flags(h);
+}
+
+size_t tc_field_bytes(const tc_handle* h, int which, int space) {
+    if (!h) return 0;
+    const TcDev& d = h->d;
+    if (which == TC_FIELD_MEAN_U || which == TC_FIELD_MEAN_W) return (size_t)d.Nr * sizeof(double);
+    if (which < 0 || which > TC_FIELD_ETA) return 0;
+    if (space == TC_PHYSICAL) return (size_t)d.Nr * d.Mz * d.Mt * sizeof(double);
+    return (size_t)d.Nr * d.npairs * sizeof(double2);
+}
+
+int tc_get_field(tc_handle* h, int which, int space, void* buf, size_t bytes) {
+    if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
+    if (which < 0 || which > TC_FIELD_MEAN_W || (space != TC_SPECTRAL && space != TC_PHYSICAL)) {
+        set_err("unknown field or space");
+        return TC_ERR_ARG;
+    }
+    const size_t need = tc_field_bytes(h, which, space);
+    if (bytes != need) { set_err("buffer size " + std::to_string(bytes) + " != " + std::to_string(need)); return TC_ERR_SIZE; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    TcDev& d = h->d;
+    if (which == TC_FIELD_MEAN_U || which == TC_FIELD_MEAN_W) {
+        CK(cudaMemcpyAsync(buf, which == TC_FIELD_MEAN_U ? d.U : d.W, bytes, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return TC_OK;
+    }
+    const double2* src = which == TC_FIELD_U ? d.u : which == TC_FIELD_V ? d.v : which == TC_FIELD_W ? d.w : d.eta;
+    if (space == TC_SPECTRAL) {
+        CK(cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        if (!d.phys) {
+            double* p;
+            if ((rc = dalloc(h, p, (size_t)d.Nr * d.Mz * d.Mt))) return rc;
+            d.phys = p;
+            if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+        }
+        tc_launch_to_physical(d, src, h->stream);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(buf, d.phys, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return TC_OK;
+}
+
+int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
+    if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
+    TcDev& d = h->d;
+    if (which == TC_FIELD_MEAN_U || which == TC_FIELD_MEAN_W) {
+        if (bytes != (size_t)d.Nr * sizeof(double)) { set_err("mean profile needs Nr float64"); return TC_ERR_SIZE; }
+        CK(cudaMemcpyAsync(which == TC_FIELD_MEAN_U ? d.U : d.W, buf, bytes, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->need_init = true;
+        h->phase = 0;
+        return TC_OK;
+    }
+    if (which != TC_FIELD_V && which != TC_FIELD_ETA) { set_err("only V, ETA, MEAN_U and MEAN_W can be set"); return TC_ERR_ARG; }
+    const size_t need = (size_t)d.Nr * d.npairs * sizeof(double2);
+    if (bytes != need) { set_err("buffer size " + std::to_string(bytes) + " != " + std::to_string(need)); return TC_ERR_SIZE; }
+    double2* dst = which == TC_FIELD_V ? d.v : d.eta;
+    CK(cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, h->stream));
+    // Hermitian m = 0 column, zero Nyquist slot and (0,0): small fix-up copies
+    // (2 (Nz/2 - 1) + Nh + 1 elements per radial point) done on the device.
+    std::vector<double2> col((size_t)d.Nr * d.Nz);
+    const double2* hb = static_cast<const double2*>(buf);
+    for (int r = 0; r < d.Nr; ++r)
+        for (int s = 0; s < d.Nz; ++s) col[(size_t)r * d.Nz + s] = hb[((size_t)r * d.Nz + s) * d.Nh];
+    for (int r = 0; r < d.Nr; ++r) {
+        double2* c = &col[(size_t)r * d.Nz];
+        c[0] = make_double2(0.0, 0.0);
+        c[d.Nz / 2] = make_double2(0.0, 0.0);
+        for (int n = 1; n < d.Nz / 2; ++n) c[d.Nz - n] = make_double2(c[n].x, -c[n].y);
+    }
+    CK(cudaMemcpy2DAsync(dst, d.Nh * sizeof(double2), col.data(), sizeof(double2), sizeof(double2),
+                         (size_t)d.Nr * d.Nz, cudaMemcpyHostToDevice, h->stream));
+    std::vector<double2> zero((size_t)d.Nr * d.Nh, make_double2(0.0, 0.0));
+    CK(cudaMemcpy2DAsync(dst + (size_t)(d.Nz / 2) * d.Nh, (size_t)d.npairs * sizeof(double2), zero.data(),
+                         d.Nh * sizeof(double2), d.Nh * sizeof(double2), d.Nr, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->need_init = true;
+    h->phase = 0;
+    return TC_OK;
+}
+
+int tc_torque_stats(tc_handle* h, tc_stats* out) {
+    if (!h || !out) { set_err("null handle or output"); return TC_ERR_ARG; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    TcDev& d = h->d;
+    const int N = d.Nr;
+    std::vector<double> W(N), ep(N);
+    tc_launch_energy(d, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(W.data(), d.W, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(ep.data(), d.eprof, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double* e0 = &h->S.dwall[0];
+    const double* e1 = &h->S.dwall[5];
+    double dWi = 0, dWo = 0;
+    for (int s = 0; s < 5; ++s) { dWi += e0[s] * W[s]; dWo += e1[s] * W[N - 5 + s]; }
+    const double si = std::fabs(dWi - W[0] / h->r[0]);
+    const double so = std::fabs(dWo - W[N - 1] / h->r[N - 1]);
+    out->t = h->t;
+    out->step = h->step;
+    out->G_inner = 2.0 * M_PI * h->Ri * si;
+    out->G_outer = 2.0 * M_PI * h->Ro * h->Ro / h->Ri * so;
+    out->Re_tau_inner = std::sqrt(d.nu * si) / d.nu;
+    out->Re_tau_outer = std::sqrt(d.nu * so) / d.nu;
+    // fourth-order radial quadrature with weight r (uniform grid):
+    // trapezoid with end weights 3/8, 7/6, 23/24
+    double num = 0, den = 0;
+    const double hh = (h->r[N - 1] - h->r[0]) / (N - 1);
+    for (int j = 0; j < N; ++j) {
+        double w = 1.0;
+        if (j == 0 || j == N - 1) w = 3.0 / 8.0;
+        else if (j == 1 || j == N - 2) w = 7.0 / 6.0;
+        else if (j == 2 || j == N - 3) w = 23.0 / 24.0;
+        w *= hh * h->r[j];
+        num += w * ep[j];
+        den += w;
+    }
+    out->energy = 0.5 * num / den;
+    return TC_OK;
+}
+
+size_t tc_device_bytes(const tc_handle* h) { return h ? h->dev_bytes : 0; }
+
+int tc_phase_times(tc_handle* h, int nsteps, double* ms, int nphases) {
+    if (!h || nsteps < 1 || !ms || nphases < TC_NPHASES) { set_err("invalid arguments"); return TC_ERR_ARG; }
+    if (h->phase != 0) { set_err("tc_phase_times called inside a step"); return TC_ERR_ARG; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    cudaEvent_t ev[TC_NPHASES + 1];
+    for (int i = 0; i <= TC_NPHASES; ++i) CK(cudaEventCreate(&ev[i]));
+    double acc[TC_NPHASES] = {0, 0, 0, 0, 0};
+    for (int n = 0; n < nsteps; ++n) {
+        for (int k = 0; k < 3; ++k) {
+            CK(cudaEventRecord(ev[0], h->stream));
+            for (int w = 0; w < 3; ++w) {
+                tc_launch_plane_kernel(h->d, w, h->stream);
+                CK(cudaEventRecord(ev[w + 1], h->stream));
+            }
+            tc_launch_line_phase(h->d, k, h->stream);
+            CK(cudaEventRecord(ev[4], h->stream));
+            tc_launch_mean_phase(h->d, k, h->stream);
+            CK(cudaEventRecord(ev[5], h->stream));
+            CK(cudaEventSynchronize(ev[5]));
+            for (int i = 0; i < TC_NPHASES; ++i) {
+                float t = 0;
+                CK(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+                acc[i] += t;
+            }
+        }
+        h->t += h->d.dt;
+        h->step += 1;
+    }
+    for (int i = 0; i <= TC_NPHASES; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < TC_NPHASES; ++i) ms[i] = acc[i] / (3.0 * nsteps);
+    return check_flags(h);
+}
+
+int tc_fma_peak(int device, double* fp64_tflops, double* fp32_tflops) {
+    if (!fp64_tflops || !fp32_tflops) { set_err("null output"); return TC_ERR_ARG; }
+    if (device >= 0) CK(cudaSetDevice(device));
+    CK(tc_probe_fma(fp64_tflops, fp32_tflops));
+    return TC_OK;
+}
+
+}  // extern "C"

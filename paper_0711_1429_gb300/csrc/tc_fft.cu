@@ -1,0 +1,330 @@
+// Plane phase: pseudo-spectral products of the velocity with the 3/2 rule.
+//
+// Paper: Fourier expansion in theta and z; the non-linear terms are those of
+// the primitive-variable equations (Appendix, below Eq. 3), i.e. the six
+// products uu, uv, uw, vv, vw, ww of the velocity.  They are formed in
+// physical space on an Mt x Mz = (3 Ntheta/2) x (3 Nz/2) grid, which makes
+// the quadratic products free of aliasing on the retained modes.
+//
+// Three kernels per substep:
+//   k_zinv  : per (field, r, tile of C azimuthal columns): complex inverse
+//             FFT in z, Nz retained slots zero-padded to Mz.
+//   k_rows  : per (r, z-row): inverse real FFT in theta of u, v, w (packed as
+//             u + i v and w), the six products, forward real FFTs of the
+//             products packed in pairs, truncation to the Nh retained columns.
+//   k_zfwd  : per (product, r, tile): forward complex FFT in z, truncation to
+//             the Nz slots and scaling by 1/(Mt Mz).
+// All transforms are mixed-radix (4, 3, 2) Stockham FFTs in shared memory.
+// Template parameter T is the arithmetic type (double, or float in the
+// mixed-precision form).
+#include "tc_internal.h"
+
+template <typename T> struct V2;
+template <> struct V2<double> { typedef double2 t; };
+template <> struct V2<float> { typedef float2 t; };
+
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+// a * w (SIGN < 0) or a * conj(w) (SIGN > 0); w is a forward twiddle.
+template <int SIGN, typename C> __device__ __forceinline__ C c_tw(C a, C w) {
+    C r;
+    if (SIGN < 0) { r.x = a.x * w.x - a.y * w.y; r.y = a.x * w.y + a.y * w.x; }
+    else          { r.x = a.x * w.x + a.y * w.y; r.y = a.y * w.x - a.x * w.y; }
+    return r;
+}
+// multiply by SIGN * i
+template <int SIGN, typename C> __device__ __forceinline__ C c_si(C a) {
+    C r;
+    if (SIGN < 0) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
+    return r;
+}
+
+// ncols transforms of length pl.M stored contiguously in buf0 (column c at
+// c*M).  Returns the buffer that holds the result (buf0 or buf1).
+// Each stage: butterfly j of a column reads src[j + r*M/R], applies the
+// twiddles exp(SIGN 2 pi i r (j mod Ns)/(Ns R)), an R-point DFT, and writes
+// dst[(j/Ns) Ns R + (j mod Ns) + r Ns]  (Stockham auto-sort).
+template <typename T, int SIGN>
+__device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<T>::t* buf1,
+                                           int ncols, const FftPlan& pl,
+                                           const typename V2<T>::t* __restrict__ tw) {
+    typedef typename V2<T>::t C;
+    C* src = buf0;
+    C* dst = buf1;
+    const int M = pl.M;
+    for (int s = 0; s < pl.nst; ++s) {
+        const int R = pl.R[s], Ns = pl.Ns[s];
+        const int nb = M / R;
+        const C* tws = tw + pl.twoff[s];
+        for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
+            const int col = b / nb;
+            const int j = b - col * nb;
+            const int jm = j % Ns;
+            const C* sc = src + col * M;
+            C* dc = dst + col * M + (j / Ns) * Ns * R + jm;
+            if (R == 4) {
+                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb], v3 = sc[j + 3 * nb];
+                if (Ns > 1) {
+                    const C* t = tws + jm * 3;
+                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]); v3 = c_tw<SIGN>(v3, t[2]);
+                }
+                C a0 = c_add(v0, v2), a1 = c_sub(v0, v2), a2 = c_add(v1, v3), a3 = c_si<SIGN>(c_sub(v1, v3));
+                dc[0] = c_add(a0, a2);
+                dc[Ns] = c_add(a1, a3);
+                dc[2 * Ns] = c_sub(a0, a2);
+                dc[3 * Ns] = c_sub(a1, a3);
+            } else if (R == 3) {
+                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb];
+                if (Ns > 1) {
+                    const C* t = tws + jm * 2;
+                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]);
+                }
+                const T h = (T)0.5;
+                const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
+                C sm = c_add(v1, v2), df = c_sub(v1, v2);
+                C t0; t0.x = v0.x - h * sm.x; t0.y = v0.y - h * sm.y;
+                C id = c_si<SIGN>(df); id.x *= s3; id.y *= s3;
+                dc[0] = c_add(v0, sm);
+                dc[Ns] = c_add(t0, id);
+                dc[2 * Ns] = c_sub(t0, id);
+            } else {  // R == 2
+                C v0 = sc[j], v1 = sc[j + nb];
+                if (Ns > 1) v1 = c_tw<SIGN>(v1, tws[jm]);
+                dc[0] = c_add(v0, v1);
+                dc[Ns] = c_sub(v0, v1);
+            }
+        }
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
+template <typename T> __device__ __forceinline__ const typename V2<T>::t* twz(const TcDev& d);
+template <> __device__ __forceinline__ const double2* twz<double>(const TcDev& d) { return d.twz_d; }
+template <> __device__ __forceinline__ const float2* twz<float>(const TcDev& d) { return d.twz_f; }
+template <typename T> __device__ __forceinline__ const typename V2<T>::t* twt(const TcDev& d);
+template <> __device__ __forceinline__ const double2* twt<double>(const TcDev& d) { return d.twt_d; }
+template <> __device__ __forceinline__ const float2* twt<float>(const TcDev& d) { return d.twt_f; }
+
+
+// ---- k_zinv: spectral (u, v, w) -> zbuf[f][r][q][j] ---------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict__ f0,
+                                              const double2* __restrict__ f1,
+                                              const double2* __restrict__ f2) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    const int ct = d.ztile;
+    C* buf1 = buf0 + ct * d.Mz;
+    const int j0 = blockIdx.x * ct;
+    const int r = blockIdx.y;
+    const int f = blockIdx.z;
+    const double2* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
+    const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh;
+    for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
+        const int q = idx / ct, c = idx - q * ct;
+        int s = -1;
+        if (q < Nz / 2) s = q;
+        else if (q > Mz - Nz / 2) s = Nz - (Mz - q);
+        C val; val.x = 0; val.y = 0;
+        if (s >= 0) {
+            double2 x = src[((size_t)r * Nz + s) * Nh + j0 + c];
+            val.x = (T)x.x; val.y = (T)x.y;
+        }
+        buf0[c * Mz + q] = val;
+    }
+    __syncthreads();
+    C* res = fft_stockham<T, +1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
+    for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
+        const int q = idx / ct, c = idx - q * ct;
+        out[(size_t)q * Nh + j0 + c] = res[c * Mz + q];
+    }
+}
+
+// ---- k_rows: theta transforms and products for one (r, q) row --------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows(TcDev d) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
+    C* bufA = reinterpret_cast<C*>(smem_raw);          // 3 columns
+    C* bufB = bufA + 3 * Mt;                           // 3 columns
+    const int q = blockIdx.x, r = blockIdx.y;
+    const C* zb = reinterpret_cast<const C*>(d.zbuf);
+    const C* ur = zb + (((size_t)0 * Nr + r) * Mz + q) * Nh;
+    const C* vr = zb + (((size_t)1 * Nr + r) * Mz + q) * Nh;
+    const C* wr = zb + (((size_t)2 * Nr + r) * Mz + q) * Nh;
+    // Hermitian extension: column 0 = u + i v, column 1 = w
+    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
+        C a, b;
+        a.x = 0; a.y = 0; b.x = 0; b.y = 0;
+        if (p == 0) {
+            C U = ur[0], V = vr[0], W = wr[0];
+            a.x = U.x; a.y = V.x; b.x = W.x; b.y = 0;
+        } else if (p < Nh) {
+            C U = ur[p], V = vr[p], W = wr[p];
+            a.x = U.x - V.y; a.y = U.y + V.x; b = W;
+        } else if (p > Mt - Nh) {
+            const int j = Mt - p;
+            C U = ur[j], V = vr[j], W = wr[j];
+            a.x = U.x + V.y; a.y = V.x - U.y; b.x = W.x; b.y = -W.y;
+        }
+        bufA[p] = a;
+        bufA[Mt + p] = b;
+    }
+    __syncthreads();
+    C* res = fft_stockham<T, +1>(bufA, bufB, 2, d.pt, twt<T>(d));
+    C* oth = (res == bufA) ? bufB : bufA;
+    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
+        const T u = res[p].x, v = res[p].y, w = res[Mt + p].x;
+        C b0, b1, b2;
+        b0.x = u * u; b0.y = u * v;
+        b1.x = u * w; b1.y = v * v;
+        b2.x = v * w; b2.y = w * w;
+        oth[p] = b0; oth[Mt + p] = b1; oth[2 * Mt + p] = b2;
+    }
+    __syncthreads();
+    C* out = fft_stockham<T, -1>(oth, res, 3, d.pt, twt<T>(d));
+    C* pb = reinterpret_cast<C*>(d.pbuf);
+    for (int idx = threadIdx.x; idx < 3 * Nh; idx += blockDim.x) {
+        const int c = idx / Nh, j = idx - c * Nh;
+        const C cj = out[c * Mt + j];
+        const C cm = out[c * Mt + (j == 0 ? 0 : Mt - j)];
+        C x1, x2;
+        x1.x = (T)0.5 * (cj.x + cm.x); x1.y = (T)0.5 * (cj.y - cm.y);
+        x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
+        const int p1 = 2 * c, p2 = 2 * c + 1;
+        pb[(((size_t)p1 * Nr + r) * Mz + q) * Nh + j] = x1;
+        pb[(((size_t)p2 * Nr + r) * Mz + q) * Nh + j] = x2;
+    }
+}
+
+// ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) -----------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    const int ct = d.ztile;
+    C* buf1 = buf0 + ct * d.Mz;
+    const int j0 = blockIdx.x * ct;
+    const int r = blockIdx.y;
+    const int p = blockIdx.z;
+    const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh, Nr = d.Nr;
+    const C* in = reinterpret_cast<const C*>(d.pbuf) + ((size_t)p * Nr + r) * Mz * Nh;
+    for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
+        const int q = idx / ct, c = idx - q * ct;
+        buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
+    }
+    __syncthreads();
+    C* res = fft_stockham<T, -1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    const T scale = (T)(1.0 / ((double)d.Mt * (double)d.Mz));
+    C* outp = reinterpret_cast<C*>(d.prod) + ((size_t)p * Nr + r) * Nz * Nh;
+    for (int idx = threadIdx.x; idx < ct * Nz; idx += blockDim.x) {
+        const int s = idx / ct, c = idx - s * ct;
+        C val; val.x = 0; val.y = 0;
+        if (s != Nz / 2) {
+            const int n = s < Nz / 2 ? s : s - Nz;
+            const int qq = n >= 0 ? n : Mz + n;
+            val = res[c * Mz + qq];
+            val.x *= scale; val.y *= scale;
+        }
+        outp[(size_t)s * Nh + j0 + c] = val;
+    }
+}
+
+// ---- physical output of one field (float64) ---------------------------------
+__global__ void __launch_bounds__(256) k_rows_phys(TcDev d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz;
+    double2* bufA = reinterpret_cast<double2*>(smem_raw);
+    double2* bufB = bufA + Mt;
+    const int q = blockIdx.x, r = blockIdx.y;
+    const double2* fr = reinterpret_cast<const double2*>(d.zbuf) + ((size_t)r * Mz + q) * Nh;
+    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
+        double2 a = make_double2(0.0, 0.0);
+        if (p == 0) a.x = fr[0].x;
+        else if (p < Nh) a = fr[p];
+        else if (p > Mt - Nh) { a = fr[Mt - p]; a.y = -a.y; }
+        bufA[p] = a;
+    }
+    __syncthreads();
+    double2* res = fft_stockham<double, +1>(bufA, bufB, 1, d.pt, d.twt_d);
+    for (int p = threadIdx.x; p < Mt; p += blockDim.x)
+        d.phys[((size_t)r * Mz + q) * Mt + p] = res[p].x;
+}
+
+// ---- kinetic-energy profile: sum over pairs of weight |u|^2+|v|^2+|w|^2 ------
+__global__ void __launch_bounds__(256) k_energy(TcDev d) {
+    const int r = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < d.npairs; i += blockDim.x) {
+        const int j = i % d.Nh;
+        const size_t o = (size_t)r * d.npairs + i;
+        const double2 a = d.u[o], b = d.v[o], c = d.w[o];
+        const double wgt = j == 0 ? 1.0 : 2.0;
+        acc += wgt * (a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y + c.x * c.x + c.y * c.y);
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d.eprof[r] = red[0];
+}
+
+// ---- host launchers --------------------------------------------------------------
+template <typename T>
+static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
+    typedef typename V2<T>::t C;
+    const int ct = d.ztile;
+    const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
+    const size_t smr = 6 * (size_t)d.Mt * sizeof(C);
+    if (which == 0) k_zinv<T><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
+    else if (which == 1) k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
+    else k_zfwd<T><<<dim3(d.Nh / ct, d.Nr, 6), 256, smz, s>>>(d);
+}
+
+void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s) {
+    if (d.mixed) plane_kernel_t<float>(d, which, s);
+    else plane_kernel_t<double>(d, which, s);
+}
+
+void tc_launch_plane_phase(const TcDev& d, cudaStream_t s) {
+    for (int w = 0; w < 3; ++w) tc_launch_plane_kernel(d, w, s);
+}
+
+void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s) {
+    const int ct = d.ztile;
+    const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(double2);
+    TcDev dd = d;
+    // one field through slot 0 of zbuf (always float64 here)
+    k_zinv<double><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
+    k_rows_phys<<<dim3(d.Mz, d.Nr), 256, 2 * (size_t)d.Mt * sizeof(double2), s>>>(dd);
+}
+
+// Shared-memory opt-in of the FFT kernels (called once per device, before any
+// stream capture).
+cudaError_t tc_set_kernel_attributes() {
+    const int lim = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void*)k_zinv<double>); set((const void*)k_zinv<float>);
+    set((const void*)k_rows<double>); set((const void*)k_rows<float>);
+    set((const void*)k_zfwd<double>); set((const void*)k_zfwd<float>);
+    set((const void*)k_rows_phys);
+    return e;
+}
+
+void tc_launch_energy(const TcDev& d, cudaStream_t s) {
+    k_energy<<<d.Nr, 256, 0, s>>>(d);
+}

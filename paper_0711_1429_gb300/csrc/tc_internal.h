@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of libtc.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#define TC_MAX_STAGES 16
+
+// Mixed-radix (2, 3, 4) Stockham plan of one transform length M.
+// Stage s has radix R[s]; Ns[s] = product of the radices before it.
+// Forward twiddles exp(-2 pi i r jm/(Ns R)) for jm < Ns, r = 1..R-1 sit at
+// tw[twoff[s] + jm*(R-1) + r-1]; the inverse uses their conjugates.
+struct FftPlan {
+    int M;
+    int nst;
+    int R[TC_MAX_STAGES];
+    int Ns[TC_MAX_STAGES];
+    int twoff[TC_MAX_STAGES];
+    int ntw;
+};
+
+// Everything a kernel needs, passed by value.
+struct TcDev {
+    int Nr, Nz, Nh, Mt, Mz;
+    int npairs;                 // Nz * Nh
+    int mixed;                  // 1: float32 FFT/products
+    int ztile;                  // azimuthal columns per CTA of the z kernels (divides Nh)
+    double dt, nu, m0, alpha0, W_outer;
+    // RK coefficients of substep k and of the substep after it
+    double rk_alpha[3], rk_beta[3], rk_gamma[3], rk_zeta[3];
+
+    // spectral fields, complex, [Nr][Nz][Nh]
+    double2 *v, *eta, *u, *w, *Hv, *He;
+    // spectral products [6][Nr][Nz][Nh]: uu uv uw vv vw ww (double2 or float2)
+    void* prod;
+    // plane-phase intermediates: zbuf [3][Nr][Mz][Nh], pbuf [6][Nr][Mz][Nh]
+    void* zbuf;
+    void* pbuf;
+    // mean flow
+    double *U, *W, *HU, *HW;
+
+    // radial tables
+    const double* r;            // [Nr]
+    const double* rinv;         // [Nr]
+    const int* start;           // [Nr]
+    const double* d0;           // [Nr][5]
+    const double* l1;
+    const double* l2;
+    const double* l4;
+    const double* dwall;        // [2][5]
+    const double* dsol;         // [Nr][5] reversed factorisation of the d0 system
+    const double* mean_lu;      // [2 profiles][3 substeps][Nr][5] + precombination
+    const double* mean_L;       // [2][Nr][5] implicit bands of U and W rows
+    // per-pair tables, structure of arrays [..][Nr][5][npairs]
+    double* tab_luv;            // [3][Nr][5][npairs]
+    double* tab_lue;            // [3][Nr][5][npairs]
+    double* tab_lv;             // [Nr][5][npairs]
+
+    // FFT plans and twiddles (double and float copies)
+    FftPlan pz, pt;
+    const double2* twz_d;
+    const double2* twt_d;
+    const float2* twz_f;
+    const float2* twt_f;
+
+    // physical output buffer for tc_get_field (float64 [Nr][Mz][Mt])
+    double* phys;
+    // energy reduction output [Nr]
+    double* eprof;
+
+    int* flag;                  // device status flags: [0] non-finite, [1] pivot
+};
+
+// kernels launched from the host side (defined in the .cu files)
+void tc_launch_plane_phase(const TcDev& d, cudaStream_t s);
+// one kernel of the plane phase: 0 = z inverse, 1 = theta rows + products, 2 = z forward
+void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s);
+cudaError_t tc_probe_fma(double* fp64_tflops, double* fp32_tflops);
+void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s);
+void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s);
+void tc_launch_setup_tables(const TcDev& d, cudaStream_t s);
+void tc_launch_init_state(const TcDev& d, cudaStream_t s);
+void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s);
+void tc_launch_energy(const TcDev& d, cudaStream_t s);
+cudaError_t tc_set_kernel_attributes();
+cudaError_t tc_set_line_kernel_attributes();

@@ -1,0 +1,732 @@
+// Line phase: for every Fourier pair (m, alpha) the radial rows of Eq. 6 (v)
+// and Eq. 7 (eta), the banded radial solves, the Runge-Kutta memory and the
+// reconstruction of u, w from continuity; plus the mean flow (m = alpha = 0).
+//
+// One thread owns one pair and walks its radial line; the 32 threads of a
+// warp hold 32 consecutive azimuthal indices at one axial slot, so every
+// radial point is one coalesced 512-byte access per field.
+//
+// Notation (Appendix): D f = f', D_* f = f' + f/r, k^2 = alpha^2 + m^2/r^2,
+// c = 1/k^2, c1..c3 its r-derivatives, nu = 2/Re.  On row j a chain operator
+// applied to (coefficient x field) is the row stencil (d0, l1, l2, l4 for
+// I, D, D D_*, D D_* D D_*) applied to the pointwise product; D D g is
+// written D D_* g - D(g/r).
+//
+// Runge-Kutta (3 substeps, explicit third order + Crank-Nicolson): substep k
+// solves (M - beta_k dt L) x^k = H_k + gamma_k dt E(x^(k-1)) with the stored
+//   H_k = (M + alpha_k dt L) x^(k-1) + zeta_k dt E(x^(k-2)),
+// and prepares H_(k+1) = RHS_k + zeta_(k+1) dt E(x^(k-1)) + (beta_k +
+// alpha_(k+1)) dt L x^k, using M x^k = RHS_k + beta_k dt L x^k.
+#include "tc_internal.h"
+
+namespace {
+
+struct Coef { double k2, c, c1, c2, c3; };
+
+// k^2, c = 1/k^2 = r^2/g and its r-derivatives, g = alpha^2 r^2 + m^2:
+// c1 = 2 r m^2/g^2, c2 = 2 m^2 (m^2 - 3 alpha^2 r^2)/g^3,
+// c3 = -24 m^2 alpha^2 r (m^2 - alpha^2 r^2)/g^4.
+__device__ __forceinline__ Coef coef_at(double r, double rinv, double m, double al) {
+    const double m2 = m * m, a2 = al * al, r2 = r * r;
+    Coef o;
+    o.k2 = a2 + m2 * rinv * rinv;
+    const double g = a2 * r2 + m2;
+    const double gi = 1.0 / g;
+    const double gi2 = gi * gi;
+    o.c = r2 * gi;
+    o.c1 = 2.0 * r * m2 * gi2;
+    o.c2 = 2.0 * m2 * (m2 - 3.0 * a2 * r2) * gi2 * gi;
+    o.c3 = -24.0 * m2 * a2 * r * (m2 - a2 * r2) * gi2 * gi2;
+    return o;
+}
+
+__device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+// (i s) * a
+__device__ __forceinline__ double2 cimag(double s, double2 a) { return make_double2(-s * a.y, s * a.x); }
+// a + s * b
+__device__ __forceinline__ double2 caxpy(double2 a, double s, double2 b) { return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y)); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+__device__ __forceinline__ double2 ld_prod(const double2* p, size_t o) { return p[o]; }
+__device__ __forceinline__ double2 ld_prod(const float2* p, size_t o) { float2 f = p[o]; return make_double2(f.x, f.y); }
+
+// Pair index -> (n slot, j); returns false for pairs that are not evolved:
+// the axial Nyquist slot, (0,0) (mean flow) and (0, n<0) (conjugates).
+__device__ __forceinline__ bool pair_info(const TcDev& d, int pair, double& m, double& al, long long& partner) {
+    const int s = pair / d.Nh, j = pair - s * d.Nh;
+    if (s == d.Nz / 2) return false;
+    if (j == 0 && (s == 0 || s > d.Nz / 2)) return false;
+    const int n = s < d.Nz / 2 ? s : s - d.Nz;
+    m = j * d.m0;
+    al = n * d.alpha0;
+    partner = (j == 0) ? (long long)(d.Nz - s) * d.Nh : -1;
+    return true;
+}
+
+#define TAB(base, k, row, comp) (base)[((size_t)((k) * d.Nr + (row)) * 5 + (comp)) * d.npairs + pair]
+
+// Reduced band row on the unknowns 1..Nr-2: entries on columns j-2..j+2.
+struct Row5 { double a, b, dd, c, e; };
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Band of the v rows (interior j = 2..Nr-3), entry s multiplies v_{j-2+s}:
+//   mass      M = d0 - l2 c + l1 c1
+//   implicit  L = nu [2 l2 - l4 c + l1 (c2/r + c3 - c1/r^2 - 2 m^2 c/r^3)
+//                     - 2 l2 c1/r - d0 k^2]
+// (Eq. 6 with D_1 read as D and D[(1/r) DD(1/k^2) v] read as D[(c2/r) v]).
+__device__ void v_band(const TcDev& d, int j, double m, double al, double* M5, double* L5) {
+    for (int s = 0; s < 5; ++s) {
+        const int i = j - 2 + s;
+        const double r = d.r[i], ri = d.rinv[i];
+        const Coef q = coef_at(r, ri, m, al);
+        const double w0 = d.d0[j * 5 + s], w1 = d.l1[j * 5 + s], w2 = d.l2[j * 5 + s], w4 = d.l4[j * 5 + s];
+        M5[s] = w0 - w2 * q.c + w1 * q.c1;
+        L5[s] = d.nu * (2.0 * w2 - w4 * q.c
+                        + w1 * (q.c2 * ri + q.c3 - q.c1 * ri * ri - 2.0 * m * m * q.c * ri * ri * ri)
+                        - 2.0 * w2 * q.c1 * ri - w0 * q.k2);
+    }
+}
+
+// eta rows j = 1..Nr-2: mass d0, implicit nu (l2 - d0 k^2), from start[j].
+__device__ void eta_band(const TcDev& d, int j, double m, double al, double* L5) {
+    const int st = d.start[j];
+    for (int s = 0; s < 5; ++s) {
+        const int i = st + s;
+        const double ri = d.rinv[i];
+        const double k2 = al * al + m * m * ri * ri;
+        L5[s] = d.nu * (d.l2[j * 5 + s] - d.d0[j * 5 + s] * k2);
+    }
+}
+
+// Pentadiagonal LU without pivoting of the reduced system on unknowns
+// 1..Nr-2, rows produced by `row(i)`; stores per row (m2, m1, 1/diag, c', e)
+// and returns false on a vanishing pivot.
+template <typename RowFn>
+__device__ bool band_lu(const TcDev& d, double* tab, int k, int pair, RowFn row) {
+    double p2d = 1, p2c = 0, p2e = 0, p1d = 1, p1c = 0, p1e = 0;
+    bool ok = true;
+    for (int i = 1; i <= d.Nr - 2; ++i) {
+        Row5 R = row(i);
+        const double scale = fabs(R.a) + fabs(R.b) + fabs(R.dd) + fabs(R.c) + fabs(R.e);
+        const double m2 = (i >= 3) ? R.a / p2d : 0.0;
+        double b = R.b - m2 * p2c;
+        double dd = R.dd - m2 * p2e;
+        const double m1 = (i >= 2) ? b / p1d : 0.0;
+        dd = dd - m1 * p1c;
+        const double cc = R.c - m1 * p1e;
+        if (!(fabs(dd) > 1e-13 * scale)) ok = false;
+        TAB(tab, k, i, 0) = m2;
+        TAB(tab, k, i, 1) = m1;
+        TAB(tab, k, i, 2) = 1.0 / dd;
+        TAB(tab, k, i, 3) = cc;
+        TAB(tab, k, i, 4) = R.e;
+        p2d = p1d; p2c = p1c; p2e = p1e;
+        p1d = dd; p1c = cc; p1e = R.e;
+    }
+    return ok;
+}
+
+// Per-pair tables: LU factors of (M - beta_k dt L) for v and eta, k = 0..2,
+// with the boundary rows folded in, and the implicit band L of the v rows.
+__global__ void __launch_bounds__(128) k_setup(TcDev d) {
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pair >= d.npairs) return;
+    double m, al;
+    long long partner;
+    if (!pair_info(d, pair, m, al, partner)) return;
+    const int N = d.Nr;
+    const double* e0 = d.dwall;       // D at r_0 on points 0..4
+    const double* e1 = d.dwall + 5;   // D at r_{N-1} on points N-5..N-1
+    bool ok = true;
+    // implicit band of the v rows (substep independent)
+    for (int j = 2; j <= N - 3; ++j) {
+        double M5[5], L5[5];
+        v_band(d, j, m, al, M5, L5);
+        for (int s = 0; s < 5; ++s) TAB(d.tab_lv, 0, j, s) = L5[s];
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double bdt = d.rk_beta[k] * d.dt;
+        // ---- v system ----
+        auto vrow_full = [&](int j, double* A) {
+            double M5[5], L5[5];
+            v_band(d, j, m, al, M5, L5);
+            for (int s = 0; s < 5; ++s) A[s] = M5[s] - bdt * L5[s];
+        };
+        double A2[5], A3[5];
+        vrow_full(2, A2);
+        vrow_full(N - 3, A3);
+        // row 1 (Dv(r_0) = 0 on v_1..v_4) minus f * row 2 eliminates v_4
+        const double fv = e0[4] / A2[4];
+        const Row5 v1r = {0.0, 0.0, e0[1] - fv * A2[1], e0[2] - fv * A2[2], e0[3] - fv * A2[3]};
+        // row N-2 (Dv(r_{N-1}) = 0 on v_{N-5}..v_{N-2}) minus g * row N-3
+        const double gv = e1[0] / A3[0];
+        const Row5 vNr = {e1[1] - gv * A3[1], e1[2] - gv * A3[2], e1[3] - gv * A3[3], 0.0, 0.0};
+        ok &= band_lu(d, d.tab_luv, k, pair, [&](int i) -> Row5 {
+            if (i == 1) return v1r;
+            if (i == N - 2) return vNr;
+            double A[5];
+            vrow_full(i, A);
+            Row5 R = {A[0], A[1], A[2], A[3], A[4]};
+            if (i == 2) R.a = 0.0;          // column 0: v_0 = 0
+            if (i == N - 3) R.e = 0.0;      // column N-1: v_{N-1} = 0
+            return R;
+        });
+        TAB(d.tab_luv, k, 0, 0) = fv;
+        TAB(d.tab_luv, k, N - 1, 0) = gv;
+        // ---- eta system ----
+        auto erow_full = [&](int j, double* A) {
+            double L5[5];
+            eta_band(d, j, m, al, L5);
+            for (int s = 0; s < 5; ++s) A[s] = d.d0[j * 5 + s] - bdt * L5[s];
+        };
+        double B1[5], B2[5], B3[5], BN[5];
+        erow_full(1, B1);          // start 0: columns 0..4
+        erow_full(2, B2);
+        erow_full(N - 3, B3);
+        erow_full(N - 2, BN);      // start N-5
+        const double fe = B1[4] / B2[4];
+        const Row5 e1r = {0.0, 0.0, B1[1] - fe * B2[1], B1[2] - fe * B2[2], B1[3] - fe * B2[3]};
+        const double ge = BN[0] / B3[0];
+        const Row5 eNr = {BN[1] - ge * B3[1], BN[2] - ge * B3[2], BN[3] - ge * B3[3], 0.0, 0.0};
+        ok &= band_lu(d, d.tab_lue, k, pair, [&](int i) -> Row5 {
+            if (i == 1) return e1r;
+            if (i == N - 2) return eNr;
+            double A[5];
+            erow_full(i, A);
+            Row5 R = {A[0], A[1], A[2], A[3], A[4]};
+            if (i == 2) R.a = 0.0;
+            if (i == N - 3) R.e = 0.0;
+            return R;
+        });
+        TAB(d.tab_lue, k, 0, 0) = fe;
+        TAB(d.tab_lue, k, N - 1, 0) = ge;
+    }
+    if (!ok) atomicOr(d.flag + 1, 1);
+}
+
+// ---------------------------------------------------------------------------
+// u, w from v, eta (continuity and the definition of eta):
+//   Dv: 0 on rows 0, Nr-1; explicit one-sided rows 1, Nr-2; compact rows
+//       d0 . Dv = l1 . v on rows 2..Nr-3 (solved with the reversed
+//       factorisation dsol, the elimination running from the outer wall in);
+//   u = (i alpha D_*v - (i m/r) eta)/k^2,   w = ((i m/r) D_*v + i alpha eta)/k^2.
+// z_j of the elimination is kept in u[j] until the ascending pass.
+__device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, long long partner) {
+    const int N = d.Nr;
+    const size_t P = d.npairs;
+    double2 xw[5];
+    for (int s = 0; s < 5; ++s) xw[s] = cz();
+    double2 Dv1 = cz(), DvN = cz();
+    double2 z1 = cz(), z2 = cz();     // z_{jr+1}, z_{jr+2}
+    double2 r3 = cz(), r2 = cz();
+    auto known = [&](int jr, double2 rhs) -> double2 {
+        const double* w0 = d.d0 + jr * 5;
+        if (jr + 1 == N - 2) rhs = caxpy(rhs, -w0[3], DvN);
+        if (jr + 2 == N - 2) rhs = caxpy(rhs, -w0[4], DvN);
+        if (jr - 1 == 1) rhs = caxpy(rhs, -w0[1], Dv1);
+        if (jr - 2 == 1) rhs = caxpy(rhs, -w0[0], Dv1);
+        return rhs;
+    };
+    auto elim = [&](int jr, double2 rhs) {
+        const double* q = d.dsol + jr * 5;
+        double2 z = caxpy(caxpy(known(jr, rhs), -q[0], z2), -q[1], z1);
+        d.u[(size_t)jr * P + pair] = z;
+        z2 = z1;
+        z1 = z;
+    };
+    for (int i = N - 1; i >= 0; --i) {
+        for (int s = 4; s > 0; --s) xw[s] = xw[s - 1];
+        xw[0] = d.v[(size_t)i * P + pair];
+        if (i > N - 5) continue;
+        if (i == N - 5) {                       // one-sided row N-2
+            const double* w = d.l1 + (N - 2) * 5;
+            double2 acc = cz();
+            for (int s = 0; s < 5; ++s) acc = caxpy(acc, w[s], xw[s]);
+            DvN = acc;
+        }
+        const int jr = i + 2;
+        if (jr >= 2 && jr <= N - 3) {
+            const double* w = d.l1 + jr * 5;
+            double2 acc = cz();
+            for (int s = 0; s < 5; ++s) acc = caxpy(acc, w[s], xw[s]);
+            if (jr >= 4) elim(jr, acc);
+            else if (jr == 3) r3 = acc;
+            else r2 = acc;
+        }
+        if (i == 0) {                           // one-sided row 1
+            const double* w = d.l1 + 1 * 5;
+            double2 acc = cz();
+            for (int s = 0; s < 5; ++s) acc = caxpy(acc, w[s], xw[s]);
+            Dv1 = acc;
+        }
+    }
+    if (N - 3 >= 3) elim(3, r3);
+    elim(2, r2);
+    // ascending: back substitution and u, w
+    double2 p1 = cz(), p2 = cz();               // Dv_{i-1}, Dv_{i-2} among unknowns 2..N-3
+    for (int i = 0; i < N; ++i) {
+        double2 Dv;
+        if (i == 0 || i == N - 1) Dv = cz();
+        else if (i == 1) Dv = Dv1;
+        else if (i == N - 2) Dv = DvN;
+        else {
+            const double* q = d.dsol + i * 5;
+            const double2 z = d.u[(size_t)i * P + pair];
+            Dv = cscale(q[2], caxpy(caxpy(z, -q[3], p1), -q[4], p2));
+            p2 = p1;
+            p1 = Dv;
+        }
+        const double ri = d.rinv[i];
+        const Coef q = coef_at(d.r[i], ri, m, al);
+        const double2 V = d.v[(size_t)i * P + pair];
+        const double2 E = d.eta[(size_t)i * P + pair];
+        const double2 Dsv = caxpy(Dv, ri, V);
+        const double2 uu = cscale(q.c, csub(cimag(al, Dsv), cimag(m * ri, E)));
+        const double2 ww = cscale(q.c, cadd(cimag(m * ri, Dsv), cimag(al, E)));
+        d.u[(size_t)i * P + pair] = uu;
+        d.w[(size_t)i * P + pair] = ww;
+        if (partner >= 0) {
+            d.u[(size_t)i * P + partner] = cconj(uu);
+            d.w[(size_t)i * P + partner] = cconj(ww);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One substep of the line phase for every pair.
+template <typename PT>
+__global__ void __launch_bounds__(128) k_line(TcDev d, int k) {
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pair >= d.npairs) return;
+    double m, al;
+    long long partner;
+    if (!pair_info(d, pair, m, al, partner)) return;
+    const int N = d.Nr;
+    const size_t P = d.npairs;
+    const PT* prod = reinterpret_cast<const PT*>(d.prod);
+    const size_t PS = (size_t)N * P;            // product stride
+    const int kn = (k + 1) % 3;
+    const double gdt = d.rk_gamma[k] * d.dt;
+    const double zdt = d.rk_zeta[kn] * d.dt;
+    const double hdt = (d.rk_beta[k] + d.rk_alpha[kn]) * d.dt;
+    const double nu = d.nu;
+
+    // ---- forward sweep: explicit rows, right sides, forward elimination ----
+    double2 Av[5], Bv[5], Cv[5], Ae[5], Be[5];
+    for (int s = 0; s < 5; ++s) { Av[s] = Bv[s] = Cv[s] = Ae[s] = Be[s] = cz(); }
+    double2 yv1 = cz(), yv2 = cz(), ye1 = cz(), ye2 = cz();   // y_{j-1}, y_{j-2}
+    double2 rv_prev = cz(), re_prev = cz(), re_row1 = cz();
+    const double fv = TAB(d.tab_luv, k, 0, 0), gv = TAB(d.tab_luv, k, N - 1, 0);
+    const double fe = TAB(d.tab_lue, k, 0, 0), ge = TAB(d.tab_lue, k, N - 1, 0);
+
+    auto erow = [&](int j) -> double2 {          // explicit eta row j (start = i-4)
+        double2 acc = cz();
+        for (int s = 0; s < 5; ++s) {
+            acc = caxpy(acc, d.d0[j * 5 + s], Ae[s]);
+            acc = caxpy(acc, d.l1[j * 5 + s], Be[s]);
+        }
+        return acc;
+    };
+    auto vrow = [&](int j) -> double2 {
+        double2 acc = cz();
+        for (int s = 0; s < 5; ++s) {
+            acc = caxpy(acc, d.d0[j * 5 + s], Av[s]);
+            acc = caxpy(acc, d.l1[j * 5 + s], Bv[s]);
+            acc = caxpy(acc, d.l2[j * 5 + s], Cv[s]);
+        }
+        return acc;
+    };
+    // right side of row j and the partial H_(k+1) (without the L x^k term)
+    auto rhs_v = [&](int j, double2 E) -> double2 {
+        const size_t o = (size_t)j * P + pair;
+        const double2 r = caxpy(d.Hv[o], gdt, E);
+        d.Hv[o] = caxpy(r, zdt, E);
+        return r;
+    };
+    auto rhs_e = [&](int j, double2 E) -> double2 {
+        const size_t o = (size_t)j * P + pair;
+        const double2 r = caxpy(d.He[o], gdt, E);
+        d.He[o] = caxpy(r, zdt, E);
+        return r;
+    };
+    auto fwd_v = [&](int j, double2 r) {
+        const double m2 = TAB(d.tab_luv, k, j, 0), m1 = TAB(d.tab_luv, k, j, 1);
+        const double2 y = caxpy(caxpy(r, -m2, yv2), -m1, yv1);
+        d.v[(size_t)j * P + pair] = y;
+        yv2 = yv1; yv1 = y;
+    };
+    auto fwd_e = [&](int j, double2 r) {
+        const double m2 = TAB(d.tab_lue, k, j, 0), m1 = TAB(d.tab_lue, k, j, 1);
+        const double2 y = caxpy(caxpy(r, -m2, ye2), -m1, ye1);
+        d.eta[(size_t)j * P + pair] = y;
+        ye2 = ye1; ye1 = y;
+    };
+
+    for (int i = 0; i < N; ++i) {
+        for (int s = 0; s < 4; ++s) { Av[s] = Av[s + 1]; Bv[s] = Bv[s + 1]; Cv[s] = Cv[s + 1]; Ae[s] = Ae[s + 1]; Be[s] = Be[s + 1]; }
+        {
+            const size_t o = (size_t)i * P + pair;
+            const double2 uu = ld_prod(prod, o), uv = ld_prod(prod, o + PS), uw = ld_prod(prod, o + 2 * PS);
+            const double2 vv = ld_prod(prod, o + 3 * PS), vw = ld_prod(prod, o + 4 * PS), ww = ld_prod(prod, o + 5 * PS);
+            const double2 U = d.u[o], V = d.v[o], W = d.w[o];
+            const double r = d.r[i], ri = d.rinv[i], ri2 = ri * ri;
+            const Coef q = coef_at(r, ri, m, al);
+            // explicit v rows, inner functions of d0 (A), l1 (B), l2 (C)
+            double2 a = cimag(-al, uv);
+            a = caxpy(a, -ri, vv);
+            a = cadd(a, cimag(-m * ri, vw));
+            a = caxpy(a, ri, ww);
+            a = cadd(a, cimag(-2.0 * nu * m * ri2, W));
+            double2 b = cimag(al * q.c1, uv);
+            b = cadd(b, cimag(-m * (2.0 * q.c * ri2 - q.c1 * ri), vw));
+            b = caxpy(b, q.c * al * al, uu);
+            b = caxpy(b, q.c * 2.0 * al * m * ri, uw);
+            b = caxpy(b, q.c * m * m * ri2, ww);
+            b = csub(b, vv);
+            b = cadd(b, cimag(-2.0 * nu * m * q.c1 * ri2, W));
+            const double2 phi = cadd(cimag(al, U), cimag(m * ri, W));
+            double2 c = cimag(-al * q.c, uv);
+            c = cadd(c, cimag(-m * q.c * ri, vw));
+            c = caxpy(c, -3.0 * nu * q.c1, phi);
+            c = cadd(c, cimag(2.0 * nu * m * q.c * ri2, W));
+            Av[4] = a; Bv[4] = b; Cv[4] = c;
+            // explicit eta rows
+            double2 ae = cscale(m * al * ri, uu);
+            ae = cadd(ae, cimag(-2.0 * m * ri2, uv));
+            ae = caxpy(ae, m * m * ri2 - al * al, uw);
+            ae = caxpy(ae, -al * m * ri, ww);
+            ae = cadd(ae, cimag(2.0 * al * ri, vw));
+            ae = cadd(ae, cimag(4.0 * nu * m * ri2 * ri, U));
+            ae = caxpy(ae, 2.0 * nu * m * al * ri2, V);
+            double2 be = cimag(-m * ri, uv);
+            be = cadd(be, cimag(al, vw));
+            be = cadd(be, cimag(2.0 * nu * m * ri2, U));
+            Ae[4] = ae; Be[4] = be;
+        }
+        if (i < 4) continue;
+        const int j = i - 2;
+        if (i == 4) {
+            re_row1 = rhs_e(1, erow(1));
+            const double2 rv2 = rhs_v(2, vrow(2));
+            const double2 re2 = rhs_e(2, erow(2));
+            fwd_v(1, cscale(-fv, rv2));
+            fwd_v(2, rv2);
+            fwd_e(1, caxpy(re_row1, -fe, re2));
+            fwd_e(2, re2);
+            rv_prev = rv2; re_prev = re2;
+        } else if (j <= N - 3) {
+            const double2 rv = rhs_v(j, vrow(j));
+            const double2 re = rhs_e(j, erow(j));
+            fwd_v(j, rv);
+            fwd_e(j, re);
+            rv_prev = rv; re_prev = re;
+        }
+        if (i == N - 1) {
+            fwd_v(N - 2, cscale(-gv, rv_prev));
+            const double2 reN = rhs_e(N - 2, erow(N - 2));
+            fwd_e(N - 2, caxpy(reN, -ge, re_prev));
+        }
+    }
+
+    // ---- backward sweep: back substitution, H_(k+1) += (beta+alpha') dt L x ----
+    double2 xw[5], ew[5];
+    double k2w[5];
+    for (int s = 0; s < 5; ++s) { xw[s] = cz(); ew[s] = cz(); k2w[s] = 0.0; }
+    bool bad = false;
+    const double k2N = al * al + m * m * d.rinv[N - 1] * d.rinv[N - 1];
+    // point N-1 enters the window first (v = eta = 0 there)
+    xw[0] = cz(); ew[0] = cz(); k2w[0] = k2N;
+    d.v[(size_t)(N - 1) * P + pair] = cz();
+    d.eta[(size_t)(N - 1) * P + pair] = cz();
+    auto h_update = [&](int jr, bool do_v, bool do_e) {
+        const size_t o = (size_t)jr * P + pair;
+        if (do_v) {
+            double2 acc = cz();
+            for (int s = 0; s < 5; ++s) acc = caxpy(acc, TAB(d.tab_lv, 0, jr, s), xw[s]);
+            d.Hv[o] = caxpy(d.Hv[o], hdt, acc);
+        }
+        if (do_e) {
+            double2 acc = cz();
+            for (int s = 0; s < 5; ++s)
+                acc = caxpy(acc, nu * (d.l2[jr * 5 + s] - d.d0[jr * 5 + s] * k2w[s]), ew[s]);
+            d.He[o] = caxpy(d.He[o], hdt, acc);
+        }
+    };
+    for (int i = N - 2; i >= 0; --i) {
+        for (int s = 4; s > 0; --s) { xw[s] = xw[s - 1]; ew[s] = ew[s - 1]; k2w[s] = k2w[s - 1]; }
+        const double ri = d.rinv[i];
+        k2w[0] = al * al + m * m * ri * ri;
+        if (i >= 1) {
+            const size_t o = (size_t)i * P + pair;
+            const double2 yv = d.v[o], ye = d.eta[o];
+            const double2 xv = cscale(TAB(d.tab_luv, k, i, 2),
+                                      caxpy(caxpy(yv, -TAB(d.tab_luv, k, i, 3), xw[1]), -TAB(d.tab_luv, k, i, 4), xw[2]));
+            const double2 xe = cscale(TAB(d.tab_lue, k, i, 2),
+                                      caxpy(caxpy(ye, -TAB(d.tab_lue, k, i, 3), ew[1]), -TAB(d.tab_lue, k, i, 4), ew[2]));
+            bad |= !(cfinite(xv) && cfinite(xe));
+            xw[0] = xv; ew[0] = xe;
+            d.v[o] = xv; d.eta[o] = xe;
+            if (partner >= 0) {
+                d.v[(size_t)i * P + partner] = cconj(xv);
+                d.eta[(size_t)i * P + partner] = cconj(xe);
+            }
+        } else {
+            xw[0] = cz(); ew[0] = cz();
+            d.v[pair] = cz(); d.eta[pair] = cz();
+        }
+        if (i == N - 5) h_update(N - 2, false, true);          // one-sided eta row N-2
+        const int jr = i + 2;
+        if (i <= N - 5 && jr >= 2) h_update(jr, true, true);
+        if (i == 0) h_update(1, false, true);                  // one-sided eta row 1
+    }
+    if (bad) atomicOr(d.flag, 1);
+    if (partner >= 0) {
+        d.v[(size_t)(N - 1) * P + partner] = cz(); d.eta[(size_t)(N - 1) * P + partner] = cz();
+        d.v[partner] = cz(); d.eta[partner] = cz();
+    }
+    reconstruct_pair(d, pair, m, al, partner);
+}
+
+// ---------------------------------------------------------------------------
+// Initial RK memory H_1 = (M + alpha_1 dt L) x for v and eta, and u, w.
+__global__ void __launch_bounds__(128) k_init(TcDev d) {
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pair >= d.npairs) return;
+    double m, al;
+    long long partner;
+    if (!pair_info(d, pair, m, al, partner)) return;
+    const int N = d.Nr;
+    const size_t P = d.npairs;
+    const double adt = d.rk_alpha[0] * d.dt;
+    for (int j = 0; j < N; ++j) {
+        const size_t o = (size_t)j * P + pair;
+        double2 hv = cz(), he = cz();
+        if (j >= 2 && j <= N - 3) {
+            double M5[5], L5[5];
+            v_band(d, j, m, al, M5, L5);
+            for (int s = 0; s < 5; ++s) {
+                const double2 x = d.v[(size_t)(j - 2 + s) * P + pair];
+                hv = caxpy(hv, M5[s] + adt * L5[s], x);
+            }
+        }
+        if (j >= 1 && j <= N - 2) {
+            double L5[5];
+            eta_band(d, j, m, al, L5);
+            const int st = d.start[j];
+            for (int s = 0; s < 5; ++s) {
+                const double2 x = d.eta[(size_t)(st + s) * P + pair];
+                he = caxpy(he, d.d0[j * 5 + s] + adt * L5[s], x);
+            }
+        }
+        d.Hv[o] = hv;
+        d.He[o] = he;
+    }
+    reconstruct_pair(d, pair, m, al, partner);
+}
+
+// ---------------------------------------------------------------------------
+// Mean flow (m = alpha = 0), zero mean pressure gradient (Sec. 4):
+//   dW/dt = nu D D_* W - D(vw) - 2 vw/r,   dU/dt = nu (D D_* U + U/r^2) - D(uv) - uv/r,
+// rows 1..Nr-2 with Dirichlet values W(R_i) = 1, W(R_o) = Re_o/Re_i, U = 0.
+// One block: rows are assembled in parallel into shared memory, then two
+// threads run the banded eliminations (U and W) serially.
+template <typename PT>
+__global__ void __launch_bounds__(256) k_mean(TcDev d, int k, int init) {
+    extern __shared__ double sm[];
+    const int N = d.Nr;
+    double* A = sm;                    // [2][N][5] system rows
+    double* Lb = A + 2 * N * 5;        // [2][N][5] implicit rows
+    double* rhs = Lb + 2 * N * 5;      // [2][N]
+    double* x = rhs + 2 * N;           // [2][N]
+    double* Ex = x + 2 * N;            // [2][N] explicit rows
+    const PT* prod = reinterpret_cast<const PT*>(d.prod);
+    const size_t PS = (size_t)N * d.npairs;
+    const int kn = (k + 1) % 3;
+    const double bdt = d.rk_beta[k] * d.dt;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        x[j] = d.U[j];
+        x[N + j] = d.W[j];
+    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        if (j < 1 || j > N - 2) continue;
+        const int st = d.start[j];
+        double eu = 0.0, ew = 0.0;
+        for (int s = 0; s < 5; ++s) {
+            const int i = st + s;
+            const double w0 = d.d0[j * 5 + s], w1 = d.l1[j * 5 + s], w2 = d.l2[j * 5 + s];
+            const double ri = d.rinv[i];
+            Lb[(0 * N + j) * 5 + s] = d.nu * (w2 + w0 * ri * ri);   // U
+            Lb[(1 * N + j) * 5 + s] = d.nu * w2;                    // W
+            if (!init) {
+                const double uv = ld_prod(prod, (size_t)i * d.npairs + PS).x;
+                const double vw = ld_prod(prod, (size_t)i * d.npairs + 4 * PS).x;
+                eu += -w1 * uv - w0 * uv * ri;
+                ew += -w1 * vw - 2.0 * w0 * vw * ri;
+            }
+        }
+        Ex[j] = eu;
+        Ex[N + j] = ew;
+    }
+    __syncthreads();
+    if (init) {
+        // H_1 = (M + alpha_1 dt L) x, and u(0,0) = U, w(0,0) = W
+        const double adt = d.rk_alpha[0] * d.dt;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            double hu = 0.0, hw = 0.0;
+            if (j >= 1 && j <= N - 2) {
+                const int st = d.start[j];
+                for (int s = 0; s < 5; ++s) {
+                    hu += (d.d0[j * 5 + s] + adt * Lb[j * 5 + s]) * x[st + s];
+                    hw += (d.d0[j * 5 + s] + adt * Lb[(N + j) * 5 + s]) * x[N + st + s];
+                }
+            }
+            d.HU[j] = hu;
+            d.HW[j] = hw;
+            d.u[(size_t)j * d.npairs] = make_double2(x[j], 0.0);
+            d.w[(size_t)j * d.npairs] = make_double2(x[N + j], 0.0);
+        }
+        return;
+    }
+    // right sides and system rows
+    const double gdt = d.rk_gamma[k] * d.dt, zdt = d.rk_zeta[kn] * d.dt;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        for (int p = 0; p < 2; ++p) {
+            double* H = p == 0 ? d.HU : d.HW;
+            if (j >= 1 && j <= N - 2) {
+                const double rr = H[j] + gdt * Ex[p * N + j];
+                rhs[p * N + j] = rr;
+                H[j] = rr + zdt * Ex[p * N + j];
+                for (int s = 0; s < 5; ++s)
+                    A[(p * N + j) * 5 + s] = d.d0[j * 5 + s] - bdt * Lb[(p * N + j) * 5 + s];
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int p = threadIdx.x;
+        const double b0 = p == 0 ? 0.0 : 1.0;                 // value at r_0
+        const double bN = p == 0 ? 0.0 : d.W_outer;           // value at r_{N-1}
+        double* Ap = A + p * N * 5;
+        double* rp = rhs + p * N;
+        double* xp = x + p * N;
+        // move the Dirichlet columns to the right side
+        for (int j = 1; j <= N - 2; ++j) {
+            const int st = d.start[j];
+            if (st == 0) { rp[j] -= Ap[j * 5 + 0] * b0; Ap[j * 5 + 0] = 0.0; }
+            if (st + 4 == N - 1) { rp[j] -= Ap[j * 5 + 4] * bN; Ap[j * 5 + 4] = 0.0; }
+        }
+        // reduced rows on unknowns 1..N-2: (a, b, d, c, e) about the diagonal
+        auto reduced = [&](int j, double* R) {
+            const int off = d.start[j] - (j - 2);   // 0 for centred rows
+            for (int t = 0; t < 5; ++t) R[t] = 0.0;
+            for (int s = 0; s < 5; ++s) {
+                const int t = s + off;
+                if (t >= 0 && t < 5) R[t] = Ap[j * 5 + s];
+            }
+        };
+        // row 1 reaches column 4 (t = 5) and row N-2 column N-5 (t = -1):
+        // fold them with rows 2 and N-3
+        double R1[5], R2[5], R3[5], RN[5];
+        reduced(2, R2);
+        reduced(N - 3, R3);
+        {
+            const double f = Ap[1 * 5 + 4] / R2[4];
+            for (int t = 0; t < 5; ++t) R1[t] = 0.0;
+            R1[2] = Ap[1 * 5 + 1] - f * R2[1];
+            R1[3] = Ap[1 * 5 + 2] - f * R2[2];
+            R1[4] = Ap[1 * 5 + 3] - f * R2[3];
+            rp[1] -= f * rp[2];
+            const double g = Ap[(N - 2) * 5 + 0] / R3[0];
+            for (int t = 0; t < 5; ++t) RN[t] = 0.0;
+            RN[0] = Ap[(N - 2) * 5 + 1] - g * R3[1];
+            RN[1] = Ap[(N - 2) * 5 + 2] - g * R3[2];
+            RN[2] = Ap[(N - 2) * 5 + 3] - g * R3[3];
+            rp[N - 2] -= g * rp[N - 3];
+        }
+        // forward elimination (multipliers in place of the row)
+        double p2d = 1, p2c = 0, p2e = 0, p1d = 1, p1c = 0, p1e = 0;
+        double y1 = 0, y2 = 0;
+        double* U3 = Lb + p * N * 5;                     // reuse: (1/d, c, e)
+        for (int i = 1; i <= N - 2; ++i) {
+            double R[5];
+            if (i == 1) for (int t = 0; t < 5; ++t) R[t] = R1[t];
+            else if (i == N - 2) for (int t = 0; t < 5; ++t) R[t] = RN[t];
+            else reduced(i, R);
+            const double m2 = (i >= 3) ? R[0] / p2d : 0.0;
+            double b = R[1] - m2 * p2c, dd = R[2] - m2 * p2e;
+            const double m1 = (i >= 2) ? b / p1d : 0.0;
+            dd -= m1 * p1c;
+            const double cc = R[3] - m1 * p1e;
+            const double y = rp[i] - m2 * y2 - m1 * y1;
+            U3[i * 5 + 0] = 1.0 / dd; U3[i * 5 + 1] = cc; U3[i * 5 + 2] = R[4];
+            rp[i] = y;
+            y2 = y1; y1 = y;
+            p2d = p1d; p2c = p1c; p2e = p1e;
+            p1d = dd; p1c = cc; p1e = R[4];
+        }
+        double x1 = 0, x2 = 0;
+        for (int i = N - 2; i >= 1; --i) {
+            const double xi = (rp[i] - U3[i * 5 + 1] * x1 - U3[i * 5 + 2] * x2) * U3[i * 5 + 0];
+            xp[i] = xi;
+            x2 = x1; x1 = xi;
+        }
+        xp[0] = b0;
+        xp[N - 1] = bN;
+    }
+    __syncthreads();
+    // H_(k+1) += (beta_k + alpha_(k+1)) dt L x, write the profiles
+    const double hdt = (d.rk_beta[k] + d.rk_alpha[kn]) * d.dt;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        if (j >= 1 && j <= N - 2) {
+            const int st = d.start[j];
+            double lu = 0.0, lw = 0.0;
+            for (int s = 0; s < 5; ++s) {
+                const int i = st + s;
+                const double w0 = d.d0[j * 5 + s], w2 = d.l2[j * 5 + s], ri = d.rinv[i];
+                lu += d.nu * (w2 + w0 * ri * ri) * x[i];
+                lw += d.nu * w2 * x[N + i];
+            }
+            d.HU[j] += hdt * lu;
+            d.HW[j] += hdt * lw;
+        }
+        d.U[j] = x[j];
+        d.W[j] = x[N + j];
+        d.u[(size_t)j * d.npairs] = make_double2(x[j], 0.0);
+        d.w[(size_t)j * d.npairs] = make_double2(x[N + j], 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
+    k_setup<<<(d.npairs + 127) / 128, 128, 0, s>>>(d);
+}
+
+void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
+    if (d.mixed) k_line<float2><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
+    else k_line<double2><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
+}
+
+static size_t mean_smem(const TcDev& d) { return (size_t)(2 * d.Nr * 5 * 2 + 2 * d.Nr * 3) * sizeof(double); }
+
+void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s) {
+    if (d.mixed) k_mean<float2><<<1, 256, mean_smem(d), s>>>(d, k, 0);
+    else k_mean<double2><<<1, 256, mean_smem(d), s>>>(d, k, 0);
+}
+
+cudaError_t tc_set_line_kernel_attributes() {
+    const int lim = 200 * 1024;
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_mean<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)k_mean<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+void tc_launch_init_state(const TcDev& d, cudaStream_t s) {
+    k_init<<<(d.npairs + 127) / 128, 128, 0, s>>>(d);
+    k_mean<double2><<<1, 256, mean_smem(d), s>>>(d, 0, 1);
+}

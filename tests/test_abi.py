@@ -1,0 +1,44 @@
+"""Host-side checks of the C ABI (no GPU needed): the in-tree library builds
+and loads, exports every function include/tc.h declares, and rejects invalid
+arguments before touching the device."""
+import os
+
+import pytest
+
+import paper_0711_1429_gb300 as tc
+from paper_0711_1429_gb300 import build as tcbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(tc.LIB_PATH):
+        tcbuild.build()
+    return tc.lib()
+
+
+def test_exports_every_declared_function(lib):
+    names = tc.declared_functions()
+    assert "tc_create" in names and "tc_step" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("args,msg", [
+    ((5, 16, 16, 0.883, 200.0, 0.0, 1e-3), "Nr"),
+    ((33, 10, 16, 0.883, 200.0, 0.0, 1e-3), "Ntheta"),
+    ((33, 16, 14, 0.883, 200.0, 0.0, 1e-3), "Nz"),
+    ((33, 16, 16, 1.0, 200.0, 0.0, 1e-3), "radius ratio"),
+    ((33, 16, 16, 0.5, -1.0, 0.0, 1e-3), "Re_inner"),
+    ((33, 16, 16, 0.5, 100.0, 0.0, 0.0), "dt"),
+])
+def test_invalid_arguments_are_rejected(lib, args, msg):
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_create(*args)
+    assert msg in str(e.value)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.tc_step(None, 1) == tc.TC_ERR_ARG
+    assert lib.tc_get_field(None, 0, 0, None, 0) == tc.TC_ERR_ARG
+    assert lib.tc_field_bytes(None, 0, 0) == 0
+    lib.tc_destroy(None)

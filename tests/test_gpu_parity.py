@@ -1,0 +1,210 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: relative L2 1e-10 after one step and 1e-8 after 50 steps for the
+plain float64 path; the mixed form (float32 FFTs and products) is held to a
+stated error bound instead.
+"""
+import numpy as np
+import pytest
+
+import paper_0711_1429_gb300 as tc
+from oracle.grid import Case
+from oracle.rk import OracleSolver
+from oracle import fourier as fo
+from oracle import diagnostics as dg
+
+from helpers import (compare, gpu_case, gpu_state, inputs, oracle_state, relerr,
+                     workload_inputs, ensure_lib)
+
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(Nr=33, Ntheta=16, Nz=16, zeta=0.883, Re_i=200.0, Re_o=0.0, dt=1e-3)
+
+
+def _pair(cfg, v, e, precision=tc.TC_PREC_FP64):
+    c = Case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"])
+    s = OracleSolver(c)
+    s.set_fields(v=v, eta=e)
+    h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"],
+                 v=v, eta=e, precision=precision)
+    return c, s, h
+
+
+def _check(c, s, h, tol):
+    gs = gpu_state(h, c.Nr, c.Nz, c.Nh)
+    os_ = oracle_state(s)
+    err = compare(gs, os_)
+    bad = {k: e for k, e in err.items() if not e < tol}
+    assert not bad, (err, tol)
+    return err
+
+
+def test_one_step_small():
+    v, e = workload_inputs("tc-small-33x16x16")
+    c, s, h = _pair(SMALL, v, e)
+    try:
+        tc.tc_step(h, 1)
+        s.step(1)
+        _check(c, s, h, 1e-10)
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_fifty_steps_small():
+    v, e = workload_inputs("tc-small-33x16x16")
+    c, s, h = _pair(SMALL, v, e)
+    try:
+        tc.tc_step(h, 50)
+        s.step(50)
+        _check(c, s, h, 1e-8)
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_radix3_sizes_counter_rotation_ragged_tiles():
+    """Ntheta = 24, Nz = 12 (padded 36 x 18: radix 3 and 2 stages, 12
+    azimuthal columns: z tiles of 4), Nr = 17, outer wall counter-rotating."""
+    cfg = dict(Nr=17, Ntheta=24, Nz=12, zeta=0.6, Re_i=150.0, Re_o=-40.0, dt=2e-3)
+    v, e = inputs(17, 24, 12, 0.6, 11, "box", 2e-2, jmax=8, nmax=5)
+    c, s, h = _pair(cfg, v, e)
+    try:
+        tc.tc_step(h, 1)
+        s.step(1)
+        _check(c, s, h, 1e-10)
+        tc.tc_step(h, 9)
+        s.step(9)
+        _check(c, s, h, 1e-9)
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_one_step_129():
+    """Nr = 129, 128 x 128 modes, k^-2 spectrum at 0.05 rms (several warps
+    and CTAs per plane, every FFT stage radix)."""
+    cfg = dict(Nr=129, Ntheta=128, Nz=128, zeta=0.883, Re_i=3000.0, Re_o=0.0, dt=1e-3)
+    v, e = workload_inputs("tc-129x128x128")
+    c, s, h = _pair(cfg, v, e)
+    try:
+        tc.tc_step(h, 1)
+        s.step(1)
+        _check(c, s, h, 1e-10)
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_graph_step_equals_substeps_and_is_deterministic():
+    v, e = workload_inputs("tc-small-33x16x16")
+    cfg = SMALL
+    hs = [gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"],
+                   v=v, eta=e) for _ in range(3)]
+    try:
+        tc.tc_step(hs[0], 2)
+        tc.tc_advance_substeps(hs[1], 6)
+        tc.tc_step(hs[2], 2)
+        a, b, c3 = (gpu_state(h, 33, 16, 8) for h in hs)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+            assert np.array_equal(a[k], c3[k]), k
+        st = tc.tc_torque_stats(hs[1])
+        assert st["step"] == 2 and abs(st["t"] - 2e-3) < 1e-15
+    finally:
+        for h in hs:
+            tc.tc_destroy(h)
+
+
+def test_boundary_conditions_and_hermitian_symmetry():
+    cfg = dict(Nr=33, Ntheta=32, Nz=32, zeta=0.883, Re_i=800.0, Re_o=0.0, dt=2e-3)
+    v, e = inputs(33, 32, 32, 0.883, 5, "k2", 0.05)
+    c, s, h = _pair(cfg, v, e)
+    try:
+        tc.tc_step(h, 5)
+        g = gpu_state(h, 33, 32, 16)
+        for k in ("v", "eta", "u", "w"):
+            assert np.max(np.abs(g[k][0, :, 1:])) == 0 and np.max(np.abs(g[k][-1, :, 1:])) == 0, k
+        # Dv = 0 at both walls (explicit one-sided derivative), to round-off
+        dv_in = np.tensordot(s.S.dwall[0], g["v"][0:5], axes=(0, 0))
+        dv_out = np.tensordot(s.S.dwall[1], g["v"][-5:], axes=(0, 0))
+        scale = np.max(np.abs(g["v"])) * np.max(np.abs(s.S.dwall))
+        assert np.max(np.abs(dv_in)) < 1e-12 * scale and np.max(np.abs(dv_out)) < 1e-12 * scale
+        # m = 0 column Hermitian, Nyquist slot zero
+        for k in ("v", "eta", "u", "w"):
+            col = g[k][:, :, 0]
+            for n in range(1, 16):
+                assert np.array_equal(col[:, 32 - n], np.conj(col[:, n])), k
+            assert np.max(np.abs(g[k][:, 16, :])) == 0
+        assert np.max(np.abs(g["U"][[0, -1]])) == 0
+        assert g["W"][0] == 1.0 and g["W"][-1] == 0.0
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_physical_field_and_stats_match_oracle():
+    v, e = workload_inputs("tc-small-33x16x16")
+    c, s, h = _pair(SMALL, v, e)
+    try:
+        tc.tc_step(h, 3)
+        s.step(3)
+        u, vv, w = s.velocity()
+        for which, F in ((tc.TC_FIELD_U, u), (tc.TC_FIELD_V, vv), (tc.TC_FIELD_W, w), (tc.TC_FIELD_ETA, s.eta)):
+            P = tc.tc_get_field(h, which, tc.TC_PHYSICAL).reshape(c.Nr, c.Mz, c.Mt)
+            assert relerr(P, fo.to_physical(c, F)) < 1e-10, which
+        st = tc.tc_torque_stats(h)
+        Gi, Go = dg.torque(c, s.S, s.W)
+        ti, to = dg.re_tau(c, s.S, s.W)
+        E = dg.kinetic_energy(c, u, vv, w)
+        assert abs(st["G_inner"] - Gi) < 1e-10 * Gi and abs(st["G_outer"] - Go) < 1e-10 * Go
+        assert abs(st["Re_tau_inner"] - ti) < 1e-10 * ti and abs(st["Re_tau_outer"] - to) < 1e-10 * to
+        assert abs(st["energy"] - E) < 1e-10 * E
+        assert st["step"] == 3
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_laminar_state_stays_laminar():
+    cfg = SMALL
+    h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"])
+    try:
+        tc.tc_step(h, 10)
+        g = gpu_state(h, 33, 16, 8)
+        assert np.max(np.abs(g["v"])) == 0 and np.max(np.abs(g["eta"])) == 0
+        c = Case(33, 16, 16, 0.883, 200.0, 0.0, 1e-3)
+        z = c.zeta
+        exact = 1.0 / (1.0 - z * z) * (c.Ri / c.r - z * z * c.r / c.Ri)
+        assert np.max(np.abs(g["W"] - exact)) < 1e-6
+        st = tc.tc_torque_stats(h)
+        assert abs(st["G_inner"] - 4 * np.pi / (1 - z * z)) < 1e-4 * st["G_inner"]
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in the host input makes tc_step return TC_ERR_NONFINITE
+    (no device fault: the kernels only test values)."""
+    v, e = workload_inputs("tc-small-33x16x16")
+    v = v.copy()
+    v[10, 2, 3] = np.nan
+    cfg = SMALL
+    h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"], v=v, eta=e)
+    try:
+        with pytest.raises(tc.TcError) as ex:
+            tc.tc_step(h, 1)
+        assert ex.value.code == tc.TC_ERR_NONFINITE
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_mixed_precision_error_is_bounded():
+    """FP32 FFTs/products, FP64 radial rows and solves: error against the FP64
+    oracle after 10 steps of a 33 x 64 x 64 case with a 0.05 rms k^-2 field
+    stays below 1e-5 relative per field (it is set by float32 rounding of the
+    products, which enter only through dt * E)."""
+    cfg = dict(Nr=33, Ntheta=64, Nz=64, zeta=0.883, Re_i=3000.0, Re_o=0.0, dt=1e-3)
+    v, e = inputs(33, 64, 64, 0.883, 2, "k2", 0.05)
+    c, s, h = _pair(cfg, v, e, precision=tc.TC_PREC_MIXED)
+    try:
+        tc.tc_step(h, 10)
+        s.step(10)
+        err = _check(c, s, h, 1e-5)
+        assert max(err.values()) > 1e-12      # it really ran in float32
+    finally:
+        tc.tc_destroy(h)
