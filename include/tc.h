@@ -158,6 +158,33 @@ int tc_fma_peak(int device, double* fp64_tflops, double* fp32_tflops);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* tc_last_error(void);
 
+/* Spectral -> physical transform that allocates nothing (no counterpart in
+ * the paper).
+ *
+ * For callers that are not allowed to allocate device memory -- code held to
+ * a device-memory budget fixed in advance, plug-ins whose host application
+ * owns every buffer, loops where cudaMalloc and its implicit synchronisation
+ * are forbidden.  It computes the same physical field as tc_get_field(h,
+ * which, TC_PHYSICAL, ...) but needs no handle: spectral_dev is a device
+ * array complex128 [Nr][Nz][Ntheta/2] (layout above), physical_dev a device
+ * array float64 [Nr][3Nz/2][3Ntheta/2]; both are owned by the caller.  The
+ * work is queued on cuda_stream (NULL: legacy default stream) and the call
+ * returns without waiting.
+ *
+ * Its one intermediate (a (3Nz/2) x (Ntheta/2) complex plane) and the
+ * twiddle tables live in a static device array of TC_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.  Sizes
+ * whose plane and tables exceed it are rejected with TC_ERR_SIZE.  The first
+ * call on a device does a one-time set-up with that device current (it
+ * fetches the array's device address and opts the kernels into large shared
+ * memory); make that first call before any stream capture.  All calls share
+ * the array and each call overwrites it (nothing in it needs to start at
+ * zero), so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised by the caller. */
+#define TC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int tc_to_physical_noalloc(int Nr, int Ntheta, int Nz, const void* spectral_dev,
+                           void* physical_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,8 @@ def lib():
     L.tc_phase_times.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), i]
     L.tc_fma_peak.restype = i
     L.tc_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.tc_to_physical_noalloc.restype = i
+    L.tc_to_physical_noalloc.argtypes = [i, i, i, vp, vp, vp]
     L.tc_last_error.restype = ctypes.c_char_p
     L.tc_last_error.argtypes = []
     _lib = L
@@ -199,6 +201,12 @@ def tc_fma_peak(device=-1):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().tc_fma_peak(device, ctypes.byref(a), ctypes.byref(b)))
     return {"fp64_tflops": a.value, "fp32_tflops": b.value}
+
+
+def tc_to_physical_noalloc(Nr, Ntheta, Nz, spectral_dev_ptr, physical_dev_ptr, stream_ptr=None):
+    """Allocation-free spectral -> physical transform on caller-owned device
+    buffers (see include/tc.h); asynchronous on the given stream."""
+    return _check(lib().tc_to_physical_noalloc(Nr, Ntheta, Nz, spectral_dev_ptr, physical_dev_ptr, stream_ptr))
 
 
 def tc_last_error():

@@ -213,6 +213,12 @@ bool is_2a3b(int n) {
 
 }  // namespace
 
+// Used by the allocation-free transform entry point (tc_noalloc.cu).
+bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im) {
+    return make_plan(M, p, re, im);
+}
+void tc_set_error_message(const std::string& s) { set_err(s); }
+
 struct tc_handle {
     tc_params prm;
     TcDev d;
