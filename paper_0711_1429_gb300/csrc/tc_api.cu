@@ -315,6 +315,14 @@ int init_handle(tc_handle* h) {
     if ((rc_ = upload(h, d.l4, h->S.l4))) return rc_;
     if ((rc_ = upload(h, d.dwall, h->S.dwall))) return rc_;
     if ((rc_ = upload(h, d.dsol, h->S.dsol))) return rc_;
+    {
+        std::vector<float> f0(h->S.d0.begin(), h->S.d0.end()), f1(h->S.l1.begin(), h->S.l1.end()),
+            f2(h->S.l2.begin(), h->S.l2.end()), fr(rinv.begin(), rinv.end());
+        if ((rc_ = upload(h, d.d0f, f0))) return rc_;
+        if ((rc_ = upload(h, d.l1f, f1))) return rc_;
+        if ((rc_ = upload(h, d.l2f, f2))) return rc_;
+        if ((rc_ = upload(h, d.rinvf, fr))) return rc_;
+    }
     // FFT plans
     std::vector<ld> zr, zi, tr, ti;
     if (!make_plan(d.Mz, d.pz, zr, zi) || !make_plan(d.Mt, d.pt, tr, ti)) {
@@ -338,13 +346,13 @@ int init_handle(tc_handle* h) {
     d.v = f[0]; d.eta = f[1]; d.u = f[2]; d.w = f[3]; d.Hv = f[4]; d.He = f[5];
     for (int i = 0; i < 6; ++i) CK(cudaMemset(f[i], 0, P1 * sizeof(double2)));
     double2* pr;
-    if ((rc_ = dalloc(h, pr, 6 * P1))) return rc_;
-    CK(cudaMemset(pr, 0, 6 * P1 * sizeof(double2)));
+    if ((rc_ = dalloc(h, pr, TC_NPROD * P1))) return rc_;
+    CK(cudaMemset(pr, 0, TC_NPROD * P1 * sizeof(double2)));
     d.prod = pr;
     const size_t Z1 = (size_t)d.Nr * d.Mz * d.Nh;
     double2 *zb, *pb;
     if ((rc_ = dalloc(h, zb, 3 * Z1))) return rc_;
-    if ((rc_ = dalloc(h, pb, 6 * Z1))) return rc_;
+    if ((rc_ = dalloc(h, pb, TC_NPROD * Z1))) return rc_;
     d.zbuf = zb; d.pbuf = pb;
     double* mean;
     if ((rc_ = dalloc(h, mean, 5 * (size_t)d.Nr))) return rc_;
@@ -363,6 +371,8 @@ int init_handle(tc_handle* h) {
     if ((rc_ = dalloc(h, d.tab_luv, 3 * (size_t)d.Nr * 5 * d.npairs))) return rc_;
     if ((rc_ = dalloc(h, d.tab_lue, 3 * (size_t)d.Nr * 5 * d.npairs))) return rc_;
     if ((rc_ = dalloc(h, d.tab_lv, (size_t)d.Nr * 5 * d.npairs))) return rc_;
+    if ((rc_ = dalloc(h, d.tab_c, (size_t)d.Nr * d.npairs))) return rc_;
+    if ((rc_ = dalloc(h, d.tab_c1, (size_t)d.Nr * d.npairs))) return rc_;
     int* flag;
     if ((rc_ = dalloc(h, flag, 4))) return rc_;
     CK(cudaMemset(flag, 0, 4 * sizeof(int)));

@@ -10,8 +10,11 @@
 //   k_zinv  : per (field, r, tile of C azimuthal columns): complex inverse
 //             FFT in z, Nz retained slots zero-padded to Mz.
 //   k_rows  : per (r, z-row): inverse real FFT in theta of u, v, w (packed as
-//             u + i v and w), the six products, forward real FFTs of the
+//             u + i v and w), the products, forward real FFTs of the
 //             products packed in pairs, truncation to the Nh retained columns.
+//             The five transformed products are uu - vv, uv, uw, vw, ww - vv:
+//             the isotropic part vv of the momentum flux is a pressure
+//             gradient, which the pressure-free v and eta rows annihilate.
 //   k_zfwd  : per (product, r, tile): forward complex FFT in z, truncation to
 //             the Nz slots and scaling by 1/(Mt Mz).
 // All transforms are mixed-radix (4, 3, 2) Stockham FFTs in shared memory.
@@ -182,9 +185,10 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
         const T u = res[p].x, v = res[p].y, w = res[Mt + p].x;
         C b0, b1, b2;
-        b0.x = u * u; b0.y = u * v;
-        b1.x = u * w; b1.y = v * v;
-        b2.x = v * w; b2.y = w * w;
+        const T vv = v * v;
+        b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
+        b1.x = u * w; b1.y = v * w;          // uw, vw
+        b2.x = w * w - vv; b2.y = 0;         // ww - vv
         oth[p] = b0; oth[Mt + p] = b1; oth[2 * Mt + p] = b2;
     }
     __syncthreads();
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
         const int p1 = 2 * c, p2 = 2 * c + 1;
         pb[(((size_t)p1 * Nr + r) * Mz + q) * Nh + j] = x1;
-        pb[(((size_t)p2 * Nr + r) * Mz + q) * Nh + j] = x2;
+        if (p2 < TC_NPROD) pb[(((size_t)p2 * Nr + r) * Mz + q) * Nh + j] = x2;
     }
 }
 
@@ -288,7 +292,7 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
     const size_t smr = 6 * (size_t)d.Mt * sizeof(C);
     if (which == 0) k_zinv<T><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
     else if (which == 1) k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
-    else k_zfwd<T><<<dim3(d.Nh / ct, d.Nr, 6), 256, smz, s>>>(d);
+    else k_zfwd<T><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
 }
 
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s) {

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #define TC_MAX_STAGES 16
+#define TC_NPROD 5   // transformed products: uu-vv, uv, uw, vw, ww-vv
 
 // Mixed-radix (2, 3, 4) Stockham plan of one transform length M.
 // Stage s has radix R[s]; Ns[s] = product of the radices before it.
@@ -31,9 +32,12 @@ struct TcDev {
 
     // spectral fields, complex, [Nr][Nz][Nh]
     double2 *v, *eta, *u, *w, *Hv, *He;
-    // spectral products [6][Nr][Nz][Nh]: uu uv uw vv vw ww (double2 or float2)
+    // spectral products [TC_NPROD][Nr][Nz][Nh] (double2, or float2 in the mixed
+    // form): uu - vv, uv, uw, vw, ww - vv.  The isotropic part vv of the
+    // momentum flux is a pressure gradient, which the v and eta rows
+    // annihilate, so five transforms replace six.
     void* prod;
-    // plane-phase intermediates: zbuf [3][Nr][Mz][Nh], pbuf [6][Nr][Mz][Nh]
+    // plane-phase intermediates: zbuf [3][Nr][Mz][Nh], pbuf [TC_NPROD][Nr][Mz][Nh]
     void* zbuf;
     void* pbuf;
     // mean flow
@@ -49,12 +53,18 @@ struct TcDev {
     const double* l4;
     const double* dwall;        // [2][5]
     const double* dsol;         // [Nr][5] reversed factorisation of the d0 system
+    const float* d0f;           // float copies of d0, l1, l2 and 1/r (mixed form)
+    const float* l1f;
+    const float* l2f;
+    const float* rinvf;
     const double* mean_lu;      // [2 profiles][3 substeps][Nr][5] + precombination
     const double* mean_L;       // [2][Nr][5] implicit bands of U and W rows
     // per-pair tables, structure of arrays [..][Nr][5][npairs]
     double* tab_luv;            // [3][Nr][5][npairs]
     double* tab_lue;            // [3][Nr][5][npairs]
     double* tab_lv;             // [Nr][5][npairs]
+    double* tab_c;              // [Nr][npairs] c = 1/k^2
+    double* tab_c1;             // [Nr][npairs] c1 = dc/dr
 
     // FFT plans and twiddles (double and float copies)
     FftPlan pz, pt;

@@ -18,6 +18,7 @@
 // and prepares H_(k+1) = RHS_k + zeta_(k+1) dt E(x^(k-1)) + (beta_k +
 // alpha_(k+1)) dt L x^k, using M x^k = RHS_k + beta_k dt L x^k.
 #include "tc_internal.h"
+#include <type_traits>
 
 namespace {
 
@@ -53,6 +54,18 @@ __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isf
 
 __device__ __forceinline__ double2 ld_prod(const double2* p, size_t o) { return p[o]; }
 __device__ __forceinline__ double2 ld_prod(const float2* p, size_t o) { float2 f = p[o]; return make_double2(f.x, f.y); }
+
+// generic complex helpers for float2 / double2
+template <typename CT> __device__ __forceinline__ CT tz() { CT r; r.x = 0; r.y = 0; return r; }
+template <typename CT, typename T> __device__ __forceinline__ CT timag(T s, CT a) { CT r; r.x = -s * a.y; r.y = s * a.x; return r; }
+template <typename CT> __device__ __forceinline__ CT tadd(CT a, CT b) { CT r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename CT, typename T> __device__ __forceinline__ CT taxpy(CT a, T s, CT b) { CT r; r.x = fma(s, b.x, a.x); r.y = fma(s, b.y, a.y); return r; }
+template <typename CT, typename T> __device__ __forceinline__ CT tscale(T s, CT a) { CT r; r.x = s * a.x; r.y = s * a.y; return r; }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+template <typename CT> __device__ __forceinline__ CT from_d2(double2 a);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
 // Pair index -> (n slot, j); returns false for pairs that are not evolved:
 // the axial Nyquist slot, (0,0) (mean flow) and (0, n<0) (conjugates).
@@ -144,6 +157,11 @@ __global__ void __launch_bounds__(128) k_setup(TcDev d) {
     const double* e0 = d.dwall;       // D at r_0 on points 0..4
     const double* e1 = d.dwall + 5;   // D at r_{N-1} on points N-5..N-1
     bool ok = true;
+    for (int i = 0; i < N; ++i) {
+        const Coef q = coef_at(d.r[i], d.rinv[i], m, al);
+        d.tab_c[(size_t)i * d.npairs + pair] = q.c;
+        d.tab_c1[(size_t)i * d.npairs + pair] = q.c1;
+    }
     // implicit band of the v rows (substep independent)
     for (int j = 2; j <= N - 3; ++j) {
         double M5[5], L5[5];
@@ -283,12 +301,12 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
             p1 = Dv;
         }
         const double ri = d.rinv[i];
-        const Coef q = coef_at(d.r[i], ri, m, al);
+        const double c = d.tab_c[(size_t)i * P + pair];
         const double2 V = d.v[(size_t)i * P + pair];
         const double2 E = d.eta[(size_t)i * P + pair];
         const double2 Dsv = caxpy(Dv, ri, V);
-        const double2 uu = cscale(q.c, csub(cimag(al, Dsv), cimag(m * ri, E)));
-        const double2 ww = cscale(q.c, cadd(cimag(m * ri, Dsv), cimag(al, E)));
+        const double2 uu = cscale(c, csub(cimag(al, Dsv), cimag(m * ri, E)));
+        const double2 ww = cscale(c, cadd(cimag(m * ri, Dsv), cimag(al, E)));
         d.u[(size_t)i * P + pair] = uu;
         d.w[(size_t)i * P + pair] = ww;
         if (partner >= 0) {
@@ -300,8 +318,27 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 
 // ---------------------------------------------------------------------------
 // One substep of the line phase for every pair.
-template <typename PT>
+//
+// Explicit rows E (Eq. 6 rows 2..Nr-3, Eq. 7 rows 1..Nr-2) are sums over the
+// 5 stencil points of d0 . A + l1 . B (+ l2 . C for v), where A, B, C are
+// pointwise "inner" functions of the products and of u, v, w at that point.
+// With the five products a = uu - vv, uv, uw, vw, b = ww - vv:
+//   v:   A = -i alpha uv - i m/r vw + b/r                 - 2 i nu m w/r^2
+//        B = i alpha c1 uv - i m (2c/r^2 - c1/r) vw + c alpha^2 a
+//            + 2 c alpha m/r uw + c m^2/r^2 b             - 2 i nu m c1 w/r^2
+//        C = -i alpha c uv - i m c/r vw                   + 2 i nu m c w/r^2
+//            - 3 nu c1 (i alpha u + i m/r w)              [continuity term]
+//   eta: A = m alpha a/r - 2 i m uv/r^2 + (m^2/r^2 - alpha^2) uw - alpha m b/r
+//            + 2 i alpha vw/r + 4 i nu m u/r^3 + 2 nu m alpha v/r^2
+//        B = -i m uv/r + i alpha vw + 2 i nu m u/r^2
+// (the terms of Eqs. 6-7 regrouped per stencil; the vv parts cancel because
+// c k^2 = 1).  In the mixed form everything except the continuity term is
+// formed in float32 from the float32 products; the continuity term, the
+// right sides, the solves, the RK memory and the reconstruction are float64.
+template <bool MIXED>
 __global__ void __launch_bounds__(128) k_line(TcDev d, int k) {
+    typedef typename std::conditional<MIXED, float, double>::type T;
+    typedef typename std::conditional<MIXED, float2, double2>::type CT;
     const int pair = blockIdx.x * blockDim.x + threadIdx.x;
     if (pair >= d.npairs) return;
     double m, al;
@@ -309,38 +346,54 @@ __global__ void __launch_bounds__(128) k_line(TcDev d, int k) {
     if (!pair_info(d, pair, m, al, partner)) return;
     const int N = d.Nr;
     const size_t P = d.npairs;
-    const PT* prod = reinterpret_cast<const PT*>(d.prod);
+    const CT* prod = reinterpret_cast<const CT*>(d.prod);
     const size_t PS = (size_t)N * P;            // product stride
     const int kn = (k + 1) % 3;
     const double gdt = d.rk_gamma[k] * d.dt;
     const double zdt = d.rk_zeta[kn] * d.dt;
     const double hdt = (d.rk_beta[k] + d.rk_alpha[kn]) * d.dt;
     const double nu = d.nu;
+    const T mt = (T)m, at = (T)al, nut = (T)nu;
+    const T* w0s;
+    const T* w1s;
+    const T* w2s;
+    if constexpr (MIXED) { w0s = d.d0f; w1s = d.l1f; w2s = d.l2f; }
+    else { w0s = d.d0; w1s = d.l1; w2s = d.l2; }
 
     // ---- forward sweep: explicit rows, right sides, forward elimination ----
-    double2 Av[5], Bv[5], Cv[5], Ae[5], Be[5];
-    for (int s = 0; s < 5; ++s) { Av[s] = Bv[s] = Cv[s] = Ae[s] = Be[s] = cz(); }
+    CT Av[5], Bv[5], Cv[5], Ae[5], Be[5];
+    double2 Cp[5];                              // continuity inner function (mixed form)
+    for (int s = 0; s < 5; ++s) {
+        Av[s] = Bv[s] = Cv[s] = Ae[s] = Be[s] = tz<CT>();
+        Cp[s] = cz();
+    }
     double2 yv1 = cz(), yv2 = cz(), ye1 = cz(), ye2 = cz();   // y_{j-1}, y_{j-2}
     double2 rv_prev = cz(), re_prev = cz(), re_row1 = cz();
     const double fv = TAB(d.tab_luv, k, 0, 0), gv = TAB(d.tab_luv, k, N - 1, 0);
     const double fe = TAB(d.tab_lue, k, 0, 0), ge = TAB(d.tab_lue, k, N - 1, 0);
 
     auto erow = [&](int j) -> double2 {          // explicit eta row j (start = i-4)
-        double2 acc = cz();
+        CT acc = tz<CT>();
         for (int s = 0; s < 5; ++s) {
-            acc = caxpy(acc, d.d0[j * 5 + s], Ae[s]);
-            acc = caxpy(acc, d.l1[j * 5 + s], Be[s]);
+            acc = taxpy(acc, w0s[j * 5 + s], Ae[s]);
+            acc = taxpy(acc, w1s[j * 5 + s], Be[s]);
         }
-        return acc;
+        return to_d2(acc);
     };
     auto vrow = [&](int j) -> double2 {
-        double2 acc = cz();
+        CT acc = tz<CT>();
         for (int s = 0; s < 5; ++s) {
-            acc = caxpy(acc, d.d0[j * 5 + s], Av[s]);
-            acc = caxpy(acc, d.l1[j * 5 + s], Bv[s]);
-            acc = caxpy(acc, d.l2[j * 5 + s], Cv[s]);
+            acc = taxpy(acc, w0s[j * 5 + s], Av[s]);
+            acc = taxpy(acc, w1s[j * 5 + s], Bv[s]);
+            acc = taxpy(acc, w2s[j * 5 + s], Cv[s]);
         }
-        return acc;
+        double2 r = to_d2(acc);
+        if constexpr (MIXED) {
+            double2 cc = cz();
+            for (int s = 0; s < 5; ++s) cc = caxpy(cc, d.l2[j * 5 + s], Cp[s]);
+            r = caxpy(r, -3.0 * nu, cc);
+        }
+        return r;
     };
     // right side of row j and the partial H_(k+1) (without the L x^k term)
     auto rhs_v = [&](int j, double2 E) -> double2 {
@@ -369,44 +422,49 @@ __global__ void __launch_bounds__(128) k_line(TcDev d, int k) {
     };
 
     for (int i = 0; i < N; ++i) {
-        for (int s = 0; s < 4; ++s) { Av[s] = Av[s + 1]; Bv[s] = Bv[s + 1]; Cv[s] = Cv[s + 1]; Ae[s] = Ae[s + 1]; Be[s] = Be[s + 1]; }
+        for (int s = 0; s < 4; ++s) {
+            Av[s] = Av[s + 1]; Bv[s] = Bv[s + 1]; Cv[s] = Cv[s + 1]; Ae[s] = Ae[s + 1]; Be[s] = Be[s + 1];
+            Cp[s] = Cp[s + 1];
+        }
         {
             const size_t o = (size_t)i * P + pair;
-            const double2 uu = ld_prod(prod, o), uv = ld_prod(prod, o + PS), uw = ld_prod(prod, o + 2 * PS);
-            const double2 vv = ld_prod(prod, o + 3 * PS), vw = ld_prod(prod, o + 4 * PS), ww = ld_prod(prod, o + 5 * PS);
-            const double2 U = d.u[o], V = d.v[o], W = d.w[o];
-            const double r = d.r[i], ri = d.rinv[i], ri2 = ri * ri;
-            const Coef q = coef_at(r, ri, m, al);
-            // explicit v rows, inner functions of d0 (A), l1 (B), l2 (C)
-            double2 a = cimag(-al, uv);
-            a = caxpy(a, -ri, vv);
-            a = cadd(a, cimag(-m * ri, vw));
-            a = caxpy(a, ri, ww);
-            a = cadd(a, cimag(-2.0 * nu * m * ri2, W));
-            double2 b = cimag(al * q.c1, uv);
-            b = cadd(b, cimag(-m * (2.0 * q.c * ri2 - q.c1 * ri), vw));
-            b = caxpy(b, q.c * al * al, uu);
-            b = caxpy(b, q.c * 2.0 * al * m * ri, uw);
-            b = caxpy(b, q.c * m * m * ri2, ww);
-            b = csub(b, vv);
-            b = cadd(b, cimag(-2.0 * nu * m * q.c1 * ri2, W));
-            const double2 phi = cadd(cimag(al, U), cimag(m * ri, W));
-            double2 c = cimag(-al * q.c, uv);
-            c = cadd(c, cimag(-m * q.c * ri, vw));
-            c = caxpy(c, -3.0 * nu * q.c1, phi);
-            c = cadd(c, cimag(2.0 * nu * m * q.c * ri2, W));
-            Av[4] = a; Bv[4] = b; Cv[4] = c;
-            // explicit eta rows
-            double2 ae = cscale(m * al * ri, uu);
-            ae = cadd(ae, cimag(-2.0 * m * ri2, uv));
-            ae = caxpy(ae, m * m * ri2 - al * al, uw);
-            ae = caxpy(ae, -al * m * ri, ww);
-            ae = cadd(ae, cimag(2.0 * al * ri, vw));
-            ae = cadd(ae, cimag(4.0 * nu * m * ri2 * ri, U));
-            ae = caxpy(ae, 2.0 * nu * m * al * ri2, V);
-            double2 be = cimag(-m * ri, uv);
-            be = cadd(be, cimag(al, vw));
-            be = cadd(be, cimag(2.0 * nu * m * ri2, U));
+            const CT pa = prod[o], uv = prod[o + PS], uw = prod[o + 2 * PS], vw = prod[o + 3 * PS], pb = prod[o + 4 * PS];
+            const double2 Ud = d.u[o], Vd = d.v[o], Wd = d.w[o];
+            const CT U = from_d2<CT>(Ud), V = from_d2<CT>(Vd), W = from_d2<CT>(Wd);
+            const double cd = d.tab_c[o], c1d = d.tab_c1[o];
+            T ri, c, c1;
+            if constexpr (MIXED) { ri = d.rinvf[i]; c = (T)cd; c1 = (T)c1d; }
+            else { ri = d.rinv[i]; c = cd; c1 = c1d; }
+            const T ri2 = ri * ri;
+            // v rows
+            CT a = timag(-at, uv);
+            a = tadd(a, timag(-mt * ri, vw));
+            a = taxpy(a, ri, pb);
+            a = tadd(a, timag((T)-2 * nut * mt * ri2, W));
+            CT b = timag(at * c1, uv);
+            b = tadd(b, timag(-mt * ((T)2 * c * ri2 - c1 * ri), vw));
+            b = taxpy(b, c * at * at, pa);
+            b = taxpy(b, c * (T)2 * at * mt * ri, uw);
+            b = taxpy(b, c * mt * mt * ri2, pb);
+            b = tadd(b, timag((T)-2 * nut * mt * c1 * ri2, W));
+            CT cc = timag(-at * c, uv);
+            cc = tadd(cc, timag(-mt * c * ri, vw));
+            cc = tadd(cc, timag((T)2 * nut * mt * c * ri2, W));
+            const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
+            if constexpr (MIXED) Cp[4] = cscale(c1d, phi);
+            else cc = caxpy(cc, -3.0 * nu * c1d, phi);
+            Av[4] = a; Bv[4] = b; Cv[4] = cc;
+            // eta rows
+            CT ae = tscale(mt * at * ri, pa);
+            ae = tadd(ae, timag((T)-2 * mt * ri2, uv));
+            ae = taxpy(ae, mt * mt * ri2 - at * at, uw);
+            ae = taxpy(ae, -at * mt * ri, pb);
+            ae = tadd(ae, timag((T)2 * at * ri, vw));
+            ae = tadd(ae, timag((T)4 * nut * mt * ri2 * ri, U));
+            ae = taxpy(ae, (T)2 * nut * mt * at * ri2, V);
+            CT be = timag(-mt * ri, uv);
+            be = tadd(be, timag(at, vw));
+            be = tadd(be, timag((T)2 * nut * mt * ri2, U));
             Ae[4] = ae; Be[4] = be;
         }
         if (i < 4) continue;
@@ -440,7 +498,6 @@ __global__ void __launch_bounds__(128) k_line(TcDev d, int k) {
     for (int s = 0; s < 5; ++s) { xw[s] = cz(); ew[s] = cz(); k2w[s] = 0.0; }
     bool bad = false;
     const double k2N = al * al + m * m * d.rinv[N - 1] * d.rinv[N - 1];
-    // point N-1 enters the window first (v = eta = 0 there)
     xw[0] = cz(); ew[0] = cz(); k2w[0] = k2N;
     d.v[(size_t)(N - 1) * P + pair] = cz();
     d.eta[(size_t)(N - 1) * P + pair] = cz();
@@ -565,7 +622,7 @@ __global__ void __launch_bounds__(256) k_mean(TcDev d, int k, int init) {
             Lb[(1 * N + j) * 5 + s] = d.nu * w2;                    // W
             if (!init) {
                 const double uv = ld_prod(prod, (size_t)i * d.npairs + PS).x;
-                const double vw = ld_prod(prod, (size_t)i * d.npairs + 4 * PS).x;
+                const double vw = ld_prod(prod, (size_t)i * d.npairs + 3 * PS).x;
                 eu += -w1 * uv - w0 * uv * ri;
                 ew += -w1 * vw - 2.0 * w0 * vw * ri;
             }
@@ -708,8 +765,8 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
 }
 
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
-    if (d.mixed) k_line<float2><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
-    else k_line<double2><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
+    if (d.mixed) k_line<true><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
+    else k_line<false><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
 }
 
 static size_t mean_smem(const TcDev& d) { return (size_t)(2 * d.Nr * 5 * 2 + 2 * d.Nr * 3) * sizeof(double); }

@@ -150,3 +150,31 @@ def test_reconstruction_is_divergence_free_and_matches_eta():
     div = 1j * al * u + 1j * m / rc * w + Dsv
     assert np.max(np.abs(div)) < 1e-12 * np.max(np.abs(Dsv))
     assert np.max(np.abs(1j * m / rc * u - 1j * al * w - eta)) < 1e-12 * np.max(np.abs(eta))
+
+
+def test_isotropic_flux_changes_no_row():
+    """Adding q to uu, vv and ww adds the gradient of q to the non-linear term,
+    which the pressure-free v and eta rows must annihilate (Appendix: pressure
+    is eliminated).  The GPU path relies on it to transform 5 products
+    (uu - vv, uv, uw, vw, ww - vv) instead of 6."""
+    N = 33
+    x = radial_grid(0.883, N)
+    S = build_stencils(x)
+    rc = x.reshape(-1, 1)
+    rng = np.random.default_rng(1)
+    m = np.array([[0.0, 3.2, 6.4, 9.6]])
+    al = np.array([[1.25, 0.0, -2.5, 3.75]])
+    coef = op.coefficients(rc, m, al)
+    P = {k: rng.standard_normal((N, 4)) + 1j * rng.standard_normal((N, 4))
+         for k in ("uu", "uv", "uw", "vv", "vw", "ww")}
+    z = np.zeros((N, 4), complex)
+    q = rng.standard_normal((N, 4)) + 1j * rng.standard_normal((N, 4))
+    P2 = dict(P, uu=P["uu"] + q, vv=P["vv"] + q, ww=P["ww"] + q)
+    for f, rows in ((lambda PP: op.v_explicit(S, rc, m, al, 1.0, coef, z, z, z, PP), slice(2, N - 2)),
+                    (lambda PP: op.eta_explicit(S, rc, m, al, 1.0, z, z, z, PP), slice(1, N - 1))):
+        a, b = f(P)[rows], f(P2)[rows]
+        assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
+    # while a non-isotropic change is not annihilated
+    P3 = dict(P, uu=P["uu"] + q)
+    a, b = op.v_explicit(S, rc, m, al, 1.0, coef, z, z, z, P), op.v_explicit(S, rc, m, al, 1.0, coef, z, z, z, P3)
+    assert np.max(np.abs(a - b)[2:N - 2]) > 1e-3 * np.max(np.abs(a))
