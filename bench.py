@@ -129,21 +129,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic work per launch (the roofline numerators)
 def algorithmic(w, prec):
-    """FLOPs (5 M log2 M per complex FFT of length M) and bytes per launch of
-    each kernel, per the counts written in the design notes."""
+    """FLOPs and bytes per launch of each kernel of the step, counted for the
+    work the method needs in this formulation: a complex FFT of length M is
+    5 M log2 M flops, a real one half of that; per substep the theta rows
+    transform 3 real fields back (u, v, w) and 5 real products forward
+    (uu - vv, uv, uw, vw, ww - vv), and the z direction 3 + 5 complex
+    columns per retained azimuthal index."""
     import math
     Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
     Nh, Mt, Mz = Nt // 2, 3 * Nt // 2, 3 * Nz // 2
     f = lambda M: 5.0 * M * math.log2(M)
     cb = 8 if prec == "mixed" else 16           # bytes of one complex intermediate
     P = Nr * Nz * Nh
+    npr = 5
     return {
         "z_inverse": {"flops": 3 * Nr * Nh * f(Mz), "bytes": 3 * P * 16 + 3 * Nr * Mz * Nh * cb},
-        "theta_rows_products": {"flops": Nr * Mz * (5 * f(Mt) + 9 * Mt),
-                                "bytes": 3 * Nr * Mz * Nh * cb + 6 * Nr * Mz * Nh * cb},
-        "z_forward": {"flops": 6 * Nr * Nh * f(Mz), "bytes": 6 * Nr * Mz * Nh * cb + 6 * P * cb},
-        # line: products, u, v, w, H (read+write), new v, eta, u, w, LU and L tables
-        "line": {"flops": None, "bytes": P * (6 * cb + 48 + 64 + 64 + 120)},
+        "theta_rows_products": {"flops": Nr * Mz * (8 * 0.5 * f(Mt) + 9 * Mt),
+                                "bytes": 3 * Nr * Mz * Nh * cb + npr * Nr * Mz * Nh * cb},
+        "z_forward": {"flops": npr * Nr * Nh * f(Mz), "bytes": npr * Nr * Mz * Nh * cb + npr * P * cb},
+        # line: products, u, v, w, H (read+write), new v, eta, u, w, LU, L and c tables
+        "line": {"flops": None, "bytes": P * (npr * cb + 48 + 64 + 64 + 120 + 16)},
         "mean": {"flops": None, "bytes": Nr * 8 * 12},
     }
 

@@ -96,7 +96,8 @@ typedef struct {
 } tc_stats;
 
 /* Create a case with the default box of Sec. 4 and float64 precision.
- * Nr >= 9; Ntheta, Nz even, >= 4, of the form 2^a 3^b; 0 < zeta < 1; Re > 0;
+ * Nr >= 9; Ntheta a multiple of 4 and Nz even >= 4, both of the form 2^a 3^b;
+ * 0 < zeta < 1; Re > 0;
  * dt > 0.  The state starts as circular Couette flow (Eq. 1, W(R_o) =
  * Re_outer/Re_inner) with zero perturbation.  Returns NULL on error. */
 tc_handle* tc_create(int Nr, int Ntheta, int Nz, double radius_ratio,

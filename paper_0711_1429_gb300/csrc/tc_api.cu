@@ -324,8 +324,8 @@ int init_handle(tc_handle* h) {
         if ((rc_ = upload(h, d.rinvf, fr))) return rc_;
     }
     // FFT plans
-    std::vector<ld> zr, zi, tr, ti;
-    if (!make_plan(d.Mz, d.pz, zr, zi) || !make_plan(d.Mt, d.pt, tr, ti)) {
+    std::vector<ld> zr, zi, tr, ti, hr, hi;
+    if (!make_plan(d.Mz, d.pz, zr, zi) || !make_plan(d.Mt, d.pt, tr, ti) || !make_plan(d.Mt / 2, d.ph, hr, hi)) {
         set_err("FFT length is not of the form 2^a 3^b");
         return TC_ERR_ARG;
     }
@@ -333,6 +333,19 @@ int init_handle(tc_handle* h) {
     std::vector<float2> twz_f(zr.size()), twt_f(tr.size());
     for (size_t i = 0; i < zr.size(); ++i) { twz_d[i] = make_double2((double)zr[i], (double)zi[i]); twz_f[i] = make_float2((float)zr[i], (float)zi[i]); }
     for (size_t i = 0; i < tr.size(); ++i) { twt_d[i] = make_double2((double)tr[i], (double)ti[i]); twt_f[i] = make_float2((float)tr[i], (float)ti[i]); }
+    std::vector<double2> twh_d(hr.size()), twr_d(d.Mt / 2);
+    std::vector<float2> twh_f(hr.size()), twr_f(d.Mt / 2);
+    for (size_t i = 0; i < hr.size(); ++i) { twh_d[i] = make_double2((double)hr[i], (double)hi[i]); twh_f[i] = make_float2((float)hr[i], (float)hi[i]); }
+    for (int k = 0; k < d.Mt / 2; ++k) {
+        const ld a = -6.283185307179586476925286766559005768L * (ld)k / (ld)d.Mt;
+        twr_d[k] = make_double2((double)cosl(a), (double)sinl(a));
+        twr_f[k] = make_float2((float)cosl(a), (float)sinl(a));
+    }
+    if (twh_d.empty()) { twh_d.push_back(make_double2(1, 0)); twh_f.push_back(make_float2(1, 0)); }
+    if ((rc_ = upload(h, d.twh_d, twh_d))) return rc_;
+    if ((rc_ = upload(h, d.twh_f, twh_f))) return rc_;
+    if ((rc_ = upload(h, d.twr_d, twr_d))) return rc_;
+    if ((rc_ = upload(h, d.twr_f, twr_f))) return rc_;
     if (twz_d.empty()) { twz_d.push_back(make_double2(1, 0)); twz_f.push_back(make_float2(1, 0)); }
     if (twt_d.empty()) { twt_d.push_back(make_double2(1, 0)); twt_f.push_back(make_float2(1, 0)); }
     if ((rc_ = upload(h, d.twz_d, twz_d))) return rc_;
@@ -423,7 +436,7 @@ int ensure_graph(tc_handle* h) {
 int validate(const tc_params* p) {
     if (!p) { set_err("null parameters"); return TC_ERR_ARG; }
     if (p->Nr < 9) { set_err("Nr must be >= 9"); return TC_ERR_ARG; }
-    if (p->Ntheta < 4 || p->Ntheta % 2 || !is_2a3b(p->Ntheta)) { set_err("Ntheta must be even, >= 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
+    if (p->Ntheta < 4 || p->Ntheta % 4 || !is_2a3b(p->Ntheta)) { set_err("Ntheta must be a multiple of 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
     if (p->Nz < 4 || p->Nz % 2 || !is_2a3b(p->Nz)) { set_err("Nz must be even, >= 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
     if (!(p->radius_ratio > 0.0 && p->radius_ratio < 1.0)) { set_err("radius ratio must lie in (0, 1)"); return TC_ERR_ARG; }
     if (!(p->Re_inner > 0.0) || !std::isfinite(p->Re_outer)) { set_err("Re_inner must be > 0 and Re_outer finite"); return TC_ERR_ARG; }

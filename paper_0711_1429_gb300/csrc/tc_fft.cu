@@ -110,6 +110,12 @@ template <> __device__ __forceinline__ const float2* twz<float>(const TcDev& d) 
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twt(const TcDev& d);
 template <> __device__ __forceinline__ const double2* twt<double>(const TcDev& d) { return d.twt_d; }
 template <> __device__ __forceinline__ const float2* twt<float>(const TcDev& d) { return d.twt_f; }
+template <typename T> __device__ __forceinline__ const typename V2<T>::t* twh(const TcDev& d);
+template <> __device__ __forceinline__ const double2* twh<double>(const TcDev& d) { return d.twh_d; }
+template <> __device__ __forceinline__ const float2* twh<float>(const TcDev& d) { return d.twh_f; }
+template <typename T> __device__ __forceinline__ const typename V2<T>::t* twr(const TcDev& d);
+template <> __device__ __forceinline__ const double2* twr<double>(const TcDev& d) { return d.twr_d; }
+template <> __device__ __forceinline__ const float2* twr<float>(const TcDev& d) { return d.twr_f; }
 
 
 // ---- k_zinv: spectral (u, v, w) -> zbuf[f][r][q][j] ---------------------------
@@ -149,61 +155,107 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
 }
 
 // ---- k_rows: theta transforms and products for one (r, q) row --------------
+// Inverse: u + i v in one complex transform of length Mt (Hermitian
+// extension), w through the half-length real transform: with H = Mt/2,
+// Z_k = (X_k + conj X_{H-k}) + i (X_k - conj X_{H-k}) exp(2 pi i k/Mt),
+// z = inverse FFT_H(Z), w_{2m} = Re z_m, w_{2m+1} = Im z_m.
+// Forward: (uu - vv) + i uv and uw + i vw in two complex transforms of
+// length Mt, ww - vv through the half-length real transform:
+// z_m = b_{2m} + i b_{2m+1}, Z = FFT_H(z),
+// X_k = (Z_k + conj Z_{H-k})/2 + exp(-2 pi i k/Mt) (Z_k - conj Z_{H-k})/(2i).
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
-    C* bufA = reinterpret_cast<C*>(smem_raw);          // 3 columns
-    C* bufB = bufA + 3 * Mt;                           // 3 columns
+    const int H = Mt / 2;
+    C* fA = reinterpret_cast<C*>(smem_raw);            // 2 full columns
+    C* hA = fA + 2 * Mt;                                // 1 half column
+    C* fB = hA + H;
+    C* hB = fB + 2 * Mt;
     const int q = blockIdx.x, r = blockIdx.y;
     const C* zb = reinterpret_cast<const C*>(d.zbuf);
     const C* ur = zb + (((size_t)0 * Nr + r) * Mz + q) * Nh;
     const C* vr = zb + (((size_t)1 * Nr + r) * Mz + q) * Nh;
     const C* wr = zb + (((size_t)2 * Nr + r) * Mz + q) * Nh;
-    // Hermitian extension: column 0 = u + i v, column 1 = w
+    const C* tr = twr<T>(d);
     for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
-        C a, b;
-        a.x = 0; a.y = 0; b.x = 0; b.y = 0;
+        C a;
+        a.x = 0; a.y = 0;
         if (p == 0) {
-            C U = ur[0], V = vr[0], W = wr[0];
-            a.x = U.x; a.y = V.x; b.x = W.x; b.y = 0;
+            a.x = ur[0].x; a.y = vr[0].x;
         } else if (p < Nh) {
-            C U = ur[p], V = vr[p], W = wr[p];
-            a.x = U.x - V.y; a.y = U.y + V.x; b = W;
+            C U = ur[p], V = vr[p];
+            a.x = U.x - V.y; a.y = U.y + V.x;
         } else if (p > Mt - Nh) {
             const int j = Mt - p;
-            C U = ur[j], V = vr[j], W = wr[j];
-            a.x = U.x + V.y; a.y = V.x - U.y; b.x = W.x; b.y = -W.y;
+            C U = ur[j], V = vr[j];
+            a.x = U.x + V.y; a.y = V.x - U.y;
         }
-        bufA[p] = a;
-        bufA[Mt + p] = b;
+        fA[p] = a;
+    }
+    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+        C xk, xm;
+        xk.x = 0; xk.y = 0; xm.x = 0; xm.y = 0;
+        if (k < Nh) { xk = wr[k]; if (k == 0) xk.y = 0; }
+        const int kk = H - k;
+        if (k > 0 && kk < Nh) xm = wr[kk];
+        // E = xk + conj(xm), O = (xk - conj(xm)) exp(+2 pi i k/Mt)
+        C E, Dd, O, z;
+        E.x = xk.x + xm.x; E.y = xk.y - xm.y;
+        Dd.x = xk.x - xm.x; Dd.y = xk.y + xm.y;
+        const C t = tr[k];                     // exp(-2 pi i k/Mt)
+        O.x = Dd.x * t.x + Dd.y * t.y; O.y = Dd.y * t.x - Dd.x * t.y;
+        z.x = E.x - O.y; z.y = E.y + O.x;      // E + i O
+        hA[k] = z;
     }
     __syncthreads();
-    C* res = fft_stockham<T, +1>(bufA, bufB, 2, d.pt, twt<T>(d));
-    C* oth = (res == bufA) ? bufB : bufA;
-    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
-        const T u = res[p].x, v = res[p].y, w = res[Mt + p].x;
-        C b0, b1, b2;
-        const T vv = v * v;
-        b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
-        b1.x = u * w; b1.y = v * w;          // uw, vw
-        b2.x = w * w - vv; b2.y = 0;         // ww - vv
-        oth[p] = b0; oth[Mt + p] = b1; oth[2 * Mt + p] = b2;
+    C* r1 = fft_stockham<T, +1>(fA, fB, 1, d.pt, twt<T>(d));
+    C* r2 = fft_stockham<T, +1>(hA, hB, 1, d.ph, twh<T>(d));
+    C* o1 = (r1 == fA) ? fB : fA;
+    C* o2 = (r2 == hA) ? hB : hA;
+    for (int m = threadIdx.x; m < H; m += blockDim.x) {
+        const C w2 = r2[m];
+        T bb[2];
+        for (int e = 0; e < 2; ++e) {
+            const int p = 2 * m + e;
+            const T u = r1[p].x, v = r1[p].y, w = e ? w2.y : w2.x;
+            const T vv = v * v;
+            C b0, b1;
+            b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
+            b1.x = u * w; b1.y = v * w;          // uw, vw
+            o1[p] = b0; o1[Mt + p] = b1;
+            bb[e] = w * w - vv;                  // ww - vv
+        }
+        C z; z.x = bb[0]; z.y = bb[1];
+        o2[m] = z;
     }
     __syncthreads();
-    C* out = fft_stockham<T, -1>(oth, res, 3, d.pt, twt<T>(d));
+    C* out = fft_stockham<T, -1>(o1, r1, 2, d.pt, twt<T>(d));
+    C* out2 = fft_stockham<T, -1>(o2, r2, 1, d.ph, twh<T>(d));
     C* pb = reinterpret_cast<C*>(d.pbuf);
     for (int idx = threadIdx.x; idx < 3 * Nh; idx += blockDim.x) {
         const int c = idx / Nh, j = idx - c * Nh;
-        const C cj = out[c * Mt + j];
-        const C cm = out[c * Mt + (j == 0 ? 0 : Mt - j)];
-        C x1, x2;
-        x1.x = (T)0.5 * (cj.x + cm.x); x1.y = (T)0.5 * (cj.y - cm.y);
-        x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
-        const int p1 = 2 * c, p2 = 2 * c + 1;
-        pb[(((size_t)p1 * Nr + r) * Mz + q) * Nh + j] = x1;
-        if (p2 < TC_NPROD) pb[(((size_t)p2 * Nr + r) * Mz + q) * Nh + j] = x2;
+        if (c < 2) {
+            const C cj = out[c * Mt + j];
+            const C cm = out[c * Mt + (j == 0 ? 0 : Mt - j)];
+            C x1, x2;
+            x1.x = (T)0.5 * (cj.x + cm.x); x1.y = (T)0.5 * (cj.y - cm.y);
+            x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
+            pb[(((size_t)(2 * c) * Nr + r) * Mz + q) * Nh + j] = x1;
+            pb[(((size_t)(2 * c + 1) * Nr + r) * Mz + q) * Nh + j] = x2;
+        } else {
+            const C zk = out2[j];
+            const C zm = out2[j == 0 ? 0 : H - j];
+            C ev, od, x;
+            ev.x = (T)0.5 * (zk.x + zm.x); ev.y = (T)0.5 * (zk.y - zm.y);
+            // (Z_k - conj Z_{H-k})/(2i)
+            od.x = (T)0.5 * (zk.y + zm.y); od.y = (T)-0.5 * (zk.x - zm.x);
+            const C t = tr[j];
+            x.x = ev.x + od.x * t.x - od.y * t.y;
+            x.y = ev.y + od.x * t.y + od.y * t.x;
+            pb[(((size_t)4 * Nr + r) * Mz + q) * Nh + j] = x;
+        }
     }
 }
 
@@ -289,7 +341,7 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
     typedef typename V2<T>::t C;
     const int ct = d.ztile;
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
-    const size_t smr = 6 * (size_t)d.Mt * sizeof(C);
+    const size_t smr = 5 * (size_t)d.Mt * sizeof(C);   // 2 x (2 full + 1 half) columns
     if (which == 0) k_zinv<T><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
     else if (which == 1) k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
     else k_zfwd<T><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);

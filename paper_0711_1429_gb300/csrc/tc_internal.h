@@ -66,12 +66,18 @@ struct TcDev {
     double* tab_c;              // [Nr][npairs] c = 1/k^2
     double* tab_c1;             // [Nr][npairs] c1 = dc/dr
 
-    // FFT plans and twiddles (double and float copies)
-    FftPlan pz, pt;
+    // FFT plans and twiddles (double and float copies): pz (length Mz), pt
+    // (Mt), ph (Mt/2, the real transforms of one signal) and twr[k] =
+    // exp(-2 pi i k/Mt), k < Mt/2, for their pre/post-processing.
+    FftPlan pz, pt, ph;
     const double2* twz_d;
     const double2* twt_d;
+    const double2* twh_d;
+    const double2* twr_d;
     const float2* twz_f;
     const float2* twt_f;
+    const float2* twh_f;
+    const float2* twr_f;
 
     // physical output buffer for tc_get_field (float64 [Nr][Mz][Mt])
     double* phys;

@@ -208,3 +208,67 @@ def test_mixed_precision_error_is_bounded():
         assert max(err.values()) > 1e-12      # it really ran in float32
     finally:
         tc.tc_destroy(h)
+
+
+def test_full_size_first_substep_sampled_pairs():
+    """The 257 x 512 x 512 bench workload, in the launch configuration the
+    benchmark times: one RK substep on the GPU against the oracle on 53
+    sampled Fourier pairs (edges included) and the mean profiles.  The oracle
+    forms the products of every radial plane (in chunks of planes) and runs
+    its line phase only for the sampled pairs."""
+    from oracle.fourier import products
+    from oracle import operators as op
+    from paper_0711_1429_gb300.synthetic import WORKLOADS
+    w = WORKLOADS["tc-257x512x512"]
+    Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
+    Nh = Nt // 2
+    v, e = workload_inputs("tc-257x512x512")
+    c = Case(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"])
+    h = gpu_case(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], v=v, eta=e)
+    try:
+        tc.tc_advance_substeps(h, 1)
+        g = {"v": tc.tc_get_field(h, tc.TC_FIELD_V).reshape(Nr, Nz, Nh),
+             "eta": tc.tc_get_field(h, tc.TC_FIELD_ETA).reshape(Nr, Nz, Nh),
+             "U": tc.tc_get_field(h, tc.TC_FIELD_MEAN_U), "W": tc.tc_get_field(h, tc.TC_FIELD_MEAN_W)}
+    finally:
+        tc.tc_destroy(h)
+    # oracle: full velocity and products, then the sampled pairs' line phase
+    full = OracleSolver(c, pairs=np.zeros((Nz, Nh), dtype=bool))   # no bands; used for helpers
+    full.set_fields(v=v, eta=e)
+    mask_all = c.active_mask()
+    act = np.nonzero(mask_all)
+    m = (np.arange(Nh) * c.m0)[act[1]].reshape(1, -1)
+    al = (c.n_index() * c.alpha0).astype(float)[act[0]].reshape(1, -1)
+    k2 = op.coefficients(c.r.reshape(-1, 1), m, al)[0]
+    ua, wa = op.reconstruct_uw(full.S, c.r.reshape(-1, 1), m, al, k2, full.v[:, act[0], act[1]],
+                               full.eta[:, act[0], act[1]])
+    u = np.zeros((Nr, Nz, Nh), dtype=np.complex128)
+    ww = np.zeros_like(u)
+    u[:, act[0], act[1]] = ua
+    ww[:, act[0], act[1]] = wa
+    full._hermitian(u)
+    full._hermitian(ww)
+    del ua, wa, k2
+    u[:, 0, 0] = full.U
+    ww[:, 0, 0] = full.W
+    vv = full.v.copy()
+    P = {k: np.empty_like(vv) for k in ("uu", "uv", "uw", "vv", "vw", "ww")}
+    for r0 in range(0, Nr, 16):
+        sl = slice(r0, min(Nr, r0 + 16))
+        chunk = products(c, u[sl], vv[sl], ww[sl])
+        for k in P:
+            P[k][sl] = chunk[k]
+    del u, ww, vv
+    rng = np.random.default_rng(5)
+    sample = np.zeros((Nz, Nh), dtype=bool)
+    sample.flat[rng.choice(Nz * Nh, 48, replace=False)] = True
+    for s_, j_ in ((1, 0), (Nz // 2 - 1, 0), (Nz // 2 - 1, Nh - 1), (Nz // 2 + 1, Nh - 1), (0, 1)):
+        sample[s_, j_] = True
+    sub = OracleSolver(c, stencils=full.S, pairs=sample)
+    sub.set_fields(v=v, eta=e)
+    sub.advance(0, sub.explicit_terms(P))
+    sel = np.nonzero(sample & mask_all)
+    for key, G, O in (("v", g["v"], sub.v), ("eta", g["eta"], sub.eta)):
+        err = relerr(G[:, sel[0], sel[1]], O[:, sel[0], sel[1]])
+        assert err < 1e-10, (key, err)
+    assert relerr(g["U"], sub.U) < 1e-10 and relerr(g["W"], sub.W) < 1e-10
