@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--sample-planes", type=int, default=4)
     p.add_argument("--sample-pairs", type=int, default=1024)
+    p.add_argument("--ncases", type=int, default=64, help="batch64: number of cases")
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="served: arrival window (s)")
+    p.add_argument("--serve-rate", type=float, default=20.0, help="served: Poisson rate (1/s)")
+    p.add_argument("--budget-gb", type=float, default=150.0, help="served: device budget")
     return p.parse_args()
 
 
@@ -363,6 +367,143 @@ def run_gpu(args):
     dist.close()
 
 
+# ---------------------------------------------------------------------------
+# many cases on one GPU: the batched ensemble and the served stream
+def ensemble_case(rng, i, prec, big_prob=0.0):
+    """One case of the ensemble recipe: Nr ~ U{33..129}, Ntheta, Nz ~ U{32, 64,
+    128} independently, zeta ~ U[0.7, 0.95], Re_i ~ U[500, 3000], k^-2
+    perturbation of 0.05 rms with seed 1000 + i; with probability big_prob a
+    257 x 256 x 256 case instead."""
+    import paper_0711_1429_gb300 as tc
+    if rng.random() < big_prob:
+        Nr, Nt, Nz = 257, 256, 256
+    else:
+        Nr = int(rng.integers(33, 130))
+        Nt, Nz = (int(x) for x in rng.choice([32, 64, 128], size=2))
+    z = float(rng.uniform(0.7, 0.95))
+    Re = float(rng.uniform(500.0, 3000.0))
+    p = tc.make_params(Nr, Nt, Nz, z, Re, 0.0, 1e-3, precision=prec, autotune=1)
+    return p, (Nr, Nt, Nz, z, 1000 + i)
+
+
+def ensemble_ic(spec):
+    from paper_0711_1429_gb300.synthetic import initial_perturbation, box_defaults
+    Nr, Nt, Nz, z, seed = spec
+    m0, a0, rc = box_defaults(z)
+    return initial_perturbation(Nr, Nt, Nz, seed, "k2", 0.05, m0=m0, alpha0=a0, rc=rc)
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    import paper_0711_1429_gb300 as tc
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist(world, rank, "nccl")
+    prec = tc.TC_PREC_MIXED if args.precision == "mixed" else tc.TC_PREC_FP64
+    rng = np.random.default_rng(1000 + rank)
+    cases = [ensemble_case(rng, i, prec) for i in range(args.ncases)]
+    for p, _ in cases:
+        p.device = local
+    b = tc.tc_batch_create([p for p, _ in cases])
+    stream = torch.cuda.current_stream()
+    tc.tc_batch_set_stream(b, stream.cuda_stream)
+    gp = 0
+    for i, (p, spec) in enumerate(cases):
+        v, e = ensemble_ic(spec)
+        h = tc.tc_batch_case(b, i)
+        tc.tc_set_field(h, tc.TC_FIELD_V, v)
+        tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
+        gp += p.Nr * p.Ntheta * p.Nz
+    tc.tc_batch_step(b, max(args.warmup, 3))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        tc.tc_batch_step(b, 1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
+    total = dist.max(ev[0].elapsed_time(ev[args.steps]))
+    line = {"metric": METRIC, "value": gp * args.steps * world / (total / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"batch{args.ncases}", "cases": args.ncases, "gridpoints": gp,
+                       "precision": args.precision, "graph": "one CUDA graph per step, one branch per case",
+                       "autotune": True, "device_bytes": tc.tc_batch_device_bytes(b)},
+            "latency_ms": {"p50": statistics.median(per), "p99": per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]},
+            "gpu_launches": 15 * args.ncases * args.steps, "clocks": clk}
+    tc.tc_batch_destroy(b)
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+
+
+def run_served(args):
+    import numpy as np
+    import torch
+    import paper_0711_1429_gb300 as tc
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    prec = tc.TC_PREC_MIXED if args.precision == "mixed" else tc.TC_PREC_FP64
+    rng = np.random.default_rng(7 + rank)
+    # Poisson arrivals over the window, cases as the ensemble plus 5% 257 x 256 x 256
+    t, arrivals = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        p, spec = ensemble_case(rng, len(arrivals), prec, big_prob=0.05)
+        p.device = local
+        arrivals.append((t, p, spec, int(rng.integers(50, 501))))
+    ics = [ensemble_ic(spec) for _, _, spec, _ in arrivals]
+    s = tc.tc_server_create(int(args.budget_gb * 1e9), max_active=256, device=local)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    outs = []
+    for (ta, p, spec, n), (v, e) in zip(arrivals, ics):
+        dt_wait = ta - (time.perf_counter() - t0)
+        if dt_wait > 0:
+            time.sleep(dt_wait)
+        ov, oe = np.empty_like(v.ravel()), np.empty_like(e.ravel())
+        outs.append((ov, oe))
+        tc.tc_server_submit(s, p, v, e, n, ov, oe)
+        h2d += v.nbytes + e.nbytes
+        d2h += ov.nbytes + oe.nbytes
+    tc.tc_server_drain(s, 3600.0)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = tc.tc_server_stats(s)
+    res = tc.tc_server_poll(s, 4096)
+    tc.tc_server_destroy(s)
+    bad = [r for r in res if r["status"] != tc.TC_OK]
+    nsteps = sum(n for _, _, _, n in arrivals)
+    line = {"metric": METRIC, "value": st["gridpoint_steps"] / (st["busy_ms"] / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": int(st["steps"]), "warmup": 0, "ms_per_step": st["busy_ms"] / max(1, nsteps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "served", "requests": len(arrivals), "rate_per_s": args.serve_rate,
+                       "window_s": args.serve_seconds, "budget_gb": args.budget_gb,
+                       "precision": args.precision, "peak_active": st["peak_active"],
+                       "peak_used_gb": st["peak_used_bytes"] / 1e9, "failed": len(bad)},
+            "latency_ms": {"p50": st["step_ms_p50"], "p99": st["step_ms_p99"]},
+            "e2e": {"value": st["gridpoint_steps"] / wall, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d / max(1, nsteps), "d2h_bytes_per_step": d2h / max(1, nsteps)},
+            "gpu_launches": 15 * int(st["steps"]), "clocks": clk, "wall_s": wall}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.cpu_sample:
@@ -370,6 +511,10 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batch"):
+        run_batch(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_gpu(args)
 

@@ -82,6 +82,10 @@ typedef struct {
     double Lz;              /* axial box in h; <= 0: 5 h (Sec. 4)              */
     int precision;          /* TC_PREC_FP64 or TC_PREC_MIXED                  */
     int device;             /* CUDA device ordinal; < 0: current device        */
+    int autotune;           /* 1: time the candidate tile shapes of the z
+                               transforms and the line-phase block size at
+                               creation and keep the fastest (cached per shape
+                               class); results do not depend on the choice     */
 } tc_params;
 
 typedef struct {
@@ -158,6 +162,64 @@ int tc_fma_peak(int device, double* fp64_tflops, double* fp32_tflops);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* tc_last_error(void);
+
+/* ---- many cases on one GPU (the paper runs one case; no counterpart) ---- */
+
+/* Device bytes tc_create_ex would allocate for these parameters (0 if they
+ * are invalid); used for admission against a device-memory budget. */
+size_t tc_estimate_device_bytes(const tc_params* params);
+
+/* Batch: ncases independent cases (params[i] each, any shapes and
+ * precisions), each with its own resident state; tc_batch_step advances all
+ * of them by nsteps steps with one CUDA-graph launch per step in which every
+ * case is a concurrent branch.  Cases are reached with tc_batch_case for
+ * tc_set_field / tc_get_field / tc_torque_stats; the handle stays owned by
+ * the batch.  Results equal those of the same case stepped alone. */
+typedef struct tc_batch tc_batch;
+tc_batch* tc_batch_create(int ncases, const tc_params* params);
+tc_handle* tc_batch_case(tc_batch* b, int i);
+int tc_batch_step(tc_batch* b, int nsteps);
+int tc_batch_set_stream(tc_batch* b, void* cuda_stream);
+size_t tc_batch_device_bytes(const tc_batch* b);
+void tc_batch_destroy(tc_batch* b);
+
+/* Server: continuous batching of independent cases.  tc_server_submit queues
+ * a request (parameters, optional initial v and eta in the spectral layout,
+ * copied at submission, number of steps, optional caller-owned host buffers
+ * that receive the final v and eta); a worker thread admits queued requests
+ * while the estimated device bytes of the admitted cases stay within
+ * budget_bytes and at most max_active run, steps every admitted case on its
+ * own stream with one step in flight (cases overlap on the device), and on
+ * completion writes the outputs, frees the case and admits more.  Requests
+ * that alone exceed the budget are refused with TC_ERR_SIZE.  Thread-safe:
+ * submit / poll / drain / stats may be called from any host thread.
+ * tc_server_destroy drops queued requests and stops running ones after
+ * their current step. */
+typedef struct tc_server tc_server;
+typedef struct {
+    long long id;           /* from tc_server_submit */
+    int status;             /* TC_OK or a TC_ERR_* code */
+    long long steps;        /* steps completed */
+    tc_stats stats;         /* final torque, Re_tau, energy */
+    double queue_ms;        /* submission to admission */
+    double run_ms;          /* admission to completion */
+    double step_ms_p50;     /* per-step device latency (CUDA events) */
+    double step_ms_p99;
+} tc_result;
+typedef struct {
+    long long submitted, finished, queued, active, peak_active, steps;
+    size_t budget_bytes, used_bytes, peak_used_bytes;
+    double gridpoint_steps; /* sum over finished cases of Nr Ntheta Nz steps */
+    double busy_ms;         /* first admission to last completion */
+    double step_ms_p50, step_ms_p99;   /* over every step of finished cases */
+} tc_server_stats_t;
+tc_server* tc_server_create(size_t budget_bytes, int max_active, int device);
+int tc_server_submit(tc_server* s, const tc_params* params, const void* v0, const void* eta0,
+                     int nsteps, void* out_v, void* out_eta, long long* id);
+int tc_server_poll(tc_server* s, tc_result* out, int max_results, int* count);
+int tc_server_drain(tc_server* s, double timeout_s);
+int tc_server_stats(tc_server* s, tc_server_stats_t* out);
+void tc_server_destroy(tc_server* s);
 
 /* Spectral -> physical transform that allocates nothing (no counterpart in
  * the paper).

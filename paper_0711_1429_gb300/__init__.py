@@ -32,7 +32,7 @@ class tc_params(ctypes.Structure):
                 ("radius_ratio", ctypes.c_double), ("Re_inner", ctypes.c_double),
                 ("Re_outer", ctypes.c_double), ("dt", ctypes.c_double),
                 ("Theta", ctypes.c_double), ("Lz", ctypes.c_double),
-                ("precision", ctypes.c_int), ("device", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("device", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class tc_stats(ctypes.Structure):
@@ -40,6 +40,22 @@ class tc_stats(ctypes.Structure):
                 ("G_inner", ctypes.c_double), ("G_outer", ctypes.c_double),
                 ("Re_tau_inner", ctypes.c_double), ("Re_tau_outer", ctypes.c_double),
                 ("energy", ctypes.c_double)]
+
+
+class tc_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("steps", ctypes.c_longlong),
+                ("stats", tc_stats), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double)]
+
+
+class tc_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("finished", ctypes.c_longlong),
+                ("queued", ctypes.c_longlong), ("active", ctypes.c_longlong),
+                ("peak_active", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+                ("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("peak_used_bytes", ctypes.c_size_t), ("gridpoint_steps", ctypes.c_double),
+                ("busy_ms", ctypes.c_double), ("step_ms_p50", ctypes.c_double),
+                ("step_ms_p99", ctypes.c_double)]
 
 
 _lib = None
@@ -82,6 +98,33 @@ def lib():
     L.tc_fma_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.tc_to_physical_noalloc.restype = i
     L.tc_to_physical_noalloc.argtypes = [i, i, i, vp, vp, vp]
+    L.tc_estimate_device_bytes.restype = sz
+    L.tc_estimate_device_bytes.argtypes = [ctypes.POINTER(tc_params)]
+    L.tc_batch_create.restype = vp
+    L.tc_batch_create.argtypes = [i, ctypes.POINTER(tc_params)]
+    L.tc_batch_case.restype = vp
+    L.tc_batch_case.argtypes = [vp, i]
+    L.tc_batch_step.restype = i
+    L.tc_batch_step.argtypes = [vp, i]
+    L.tc_batch_set_stream.restype = i
+    L.tc_batch_set_stream.argtypes = [vp, vp]
+    L.tc_batch_device_bytes.restype = sz
+    L.tc_batch_device_bytes.argtypes = [vp]
+    L.tc_batch_destroy.restype = None
+    L.tc_batch_destroy.argtypes = [vp]
+    L.tc_server_create.restype = vp
+    L.tc_server_create.argtypes = [sz, i, i]
+    L.tc_server_submit.restype = i
+    L.tc_server_submit.argtypes = [vp, ctypes.POINTER(tc_params), vp, vp, i, vp, vp,
+                                   ctypes.POINTER(ctypes.c_longlong)]
+    L.tc_server_poll.restype = i
+    L.tc_server_poll.argtypes = [vp, ctypes.POINTER(tc_result), i, ctypes.POINTER(ctypes.c_int)]
+    L.tc_server_drain.restype = i
+    L.tc_server_drain.argtypes = [vp, d]
+    L.tc_server_stats.restype = i
+    L.tc_server_stats.argtypes = [vp, ctypes.POINTER(tc_server_stats_t)]
+    L.tc_server_destroy.restype = None
+    L.tc_server_destroy.argtypes = [vp]
     L.tc_last_error.restype = ctypes.c_char_p
     L.tc_last_error.argtypes = []
     _lib = L
@@ -108,9 +151,14 @@ def tc_create(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt):
     return h
 
 
+def make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0, Lz=0.0,
+                precision=TC_PREC_FP64, device=-1, autotune=0):
+    return tc_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device, autotune)
+
+
 def tc_create_ex(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0, Lz=0.0,
-                 precision=TC_PREC_FP64, device=-1):
-    p = tc_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device)
+                 precision=TC_PREC_FP64, device=-1, autotune=0):
+    p = make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device, autotune)
     h = lib().tc_create_ex(ctypes.byref(p))
     if not h:
         raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
@@ -207,6 +255,94 @@ def tc_to_physical_noalloc(Nr, Ntheta, Nz, spectral_dev_ptr, physical_dev_ptr, s
     """Allocation-free spectral -> physical transform on caller-owned device
     buffers (see include/tc.h); asynchronous on the given stream."""
     return _check(lib().tc_to_physical_noalloc(Nr, Ntheta, Nz, spectral_dev_ptr, physical_dev_ptr, stream_ptr))
+
+
+def tc_estimate_device_bytes(params):
+    return lib().tc_estimate_device_bytes(ctypes.byref(params))
+
+
+def tc_batch_create(params_list):
+    arr = (tc_params * len(params_list))(*params_list)
+    b = lib().tc_batch_create(len(params_list), arr)
+    if not b:
+        raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
+    return b
+
+
+def tc_batch_case(b, i):
+    h = lib().tc_batch_case(b, i)
+    if not h:
+        raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
+    return h
+
+
+def tc_batch_step(b, nsteps=1):
+    return _check(lib().tc_batch_step(b, nsteps))
+
+
+def tc_batch_set_stream(b, stream_ptr):
+    return _check(lib().tc_batch_set_stream(b, stream_ptr))
+
+
+def tc_batch_device_bytes(b):
+    return lib().tc_batch_device_bytes(b)
+
+
+def tc_batch_destroy(b):
+    if b:
+        lib().tc_batch_destroy(b)
+
+
+def tc_server_create(budget_bytes, max_active=64, device=-1):
+    s = lib().tc_server_create(budget_bytes, max_active, device)
+    if not s:
+        raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
+    return s
+
+
+def tc_server_submit(s, params, v0=None, eta0=None, nsteps=1, out_v=None, out_eta=None):
+    """Queue a case; v0/eta0 (complex128 spectral arrays) are copied now;
+    out_v/out_eta (C-contiguous complex128 arrays) receive the final fields and
+    must stay alive until the request finishes.  Returns the request id."""
+    ptr = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.complex128).ctypes.data
+    for o in (out_v, out_eta):
+        if o is not None and (o.dtype != np.complex128 or not o.flags.c_contiguous):
+            raise ValueError("output arrays must be C-contiguous complex128")
+    keep = [None if a is None else np.ascontiguousarray(a, dtype=np.complex128) for a in (v0, eta0)]
+    rid = ctypes.c_longlong()
+    _check(lib().tc_server_submit(s, ctypes.byref(params),
+                                  None if keep[0] is None else keep[0].ctypes.data,
+                                  None if keep[1] is None else keep[1].ctypes.data,
+                                  nsteps, None if out_v is None else out_v.ctypes.data,
+                                  None if out_eta is None else out_eta.ctypes.data, ctypes.byref(rid)))
+    return rid.value
+
+
+def tc_server_poll(s, max_results=64):
+    out = (tc_result * max_results)()
+    n = ctypes.c_int()
+    _check(lib().tc_server_poll(s, out, max_results, ctypes.byref(n)))
+    res = []
+    for r in out[:n.value]:
+        d = {k: getattr(r, k) for k, _ in tc_result._fields_ if k != "stats"}
+        d["stats"] = {k: getattr(r.stats, k) for k, _ in tc_stats._fields_}
+        res.append(d)
+    return res
+
+
+def tc_server_drain(s, timeout_s=600.0):
+    return _check(lib().tc_server_drain(s, timeout_s))
+
+
+def tc_server_stats(s):
+    st = tc_server_stats_t()
+    _check(lib().tc_server_stats(s, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in tc_server_stats_t._fields_}
+
+
+def tc_server_destroy(s):
+    if s:
+        lib().tc_server_destroy(s)
 
 
 def tc_last_error():

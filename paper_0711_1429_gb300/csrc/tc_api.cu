@@ -8,15 +8,15 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <array>
+#include <map>
+#include <mutex>
 
-#include "tc_internal.h"
-#include "../../include/tc.h"
+#include "tc_host.h"
 
 namespace {
 
 thread_local std::string g_err;
-
-void set_err(const std::string& s) { g_err = s; }
 
 #define CK(call)                                                                  \
     do {                                                                          \
@@ -76,10 +76,7 @@ ld hop(int which, int q, ld x, ld xc, ld h) {
     }
 }
 
-struct HostStencils {
-    std::vector<int> start;
-    std::vector<double> d0, l1, l2, l4, dwall, dsol;
-};
+
 
 // Stencils of the 5-point compact explicit scheme (see the oracle's notes on
 // the reading): interior rows make D D_* D D_* exact to degree 8 jointly with
@@ -213,27 +210,18 @@ bool is_2a3b(int n) {
 
 }  // namespace
 
+namespace tcx {
+void set_err(const std::string& s) { g_err = s; }
+}  // namespace tcx
+using tcx::set_err;
+
 // Used by the allocation-free transform entry point (tc_noalloc.cu).
 bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im) {
     return make_plan(M, p, re, im);
 }
 void tc_set_error_message(const std::string& s) { set_err(s); }
 
-struct tc_handle {
-    tc_params prm;
-    TcDev d;
-    cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    std::vector<void*> allocs;
-    size_t dev_bytes = 0;
-    bool need_init = true;
-    int phase = 0;                 // next substep (0..2)
-    double t = 0.0;
-    long long step = 0;
-    std::vector<double> r;
-    HostStencils S;
-    double Ri = 0, Ro = 0;
-};
+
 
 namespace {
 
@@ -269,6 +257,61 @@ void free_all(tc_handle* h) {
     h->allocs.clear();
 }
 
+// Tile autotuner: candidate azimuthal tiles of the z kernels and block sizes
+// of the line kernel are timed on the (zero) initial state, which they leave
+// unchanged, and the fastest pair is kept for the shape class (Nr, Ntheta,
+// Nz, precision).  The choice changes no arithmetic.
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, std::pair<int, int>> g_tune;
+
+int autotune(tc_handle* h) {
+    TcDev& d = h->d;
+    const std::array<int, 4> key = {d.Nr, 2 * d.Nh, d.Nz, d.mixed};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) { d.ztile = it->second.first; d.line_block = it->second.second; return TC_OK; }
+    }
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    auto timed = [&](auto fn) -> float {
+        fn();                                  // warm-up
+        cudaEventRecord(a, h->stream);
+        for (int rep = 0; rep < 3; ++rep) fn();
+        cudaEventRecord(b, h->stream);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    };
+    float best = 1e30f;
+    int best_t = d.ztile;
+    for (int t : {8, 4, 2, 1}) {
+        if (d.Nh % t) continue;
+        if (2 * (size_t)t * d.Mz * sizeof(double2) > 200 * 1024) continue;
+        d.ztile = t;
+        const float ms = timed([&] { tc_launch_plane_kernel(d, 0, h->stream); tc_launch_plane_kernel(d, 2, h->stream); });
+        if (ms < best) { best = ms; best_t = t; }
+    }
+    d.ztile = best_t;
+    best = 1e30f;
+    int best_b = d.line_block;
+    for (int bs : {64, 128, 256}) {
+        d.line_block = bs;
+        const float ms = timed([&] { tc_launch_line_phase(d, 0, h->stream); });
+        if (ms < best) { best = ms; best_b = bs; }
+    }
+    d.line_block = best_b;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CK(cudaGetLastError());
+    CK(cudaMemset(d.flag, 0, 4 * sizeof(int)));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {d.ztile, d.line_block};
+    return TC_OK;
+}
+
 int init_handle(tc_handle* h) {
     const tc_params& P = h->prm;
     TcDev& d = h->d;
@@ -281,6 +324,7 @@ int init_handle(tc_handle* h) {
     d.npairs = d.Nz * d.Nh;
     d.mixed = P.precision == TC_PREC_MIXED ? 1 : 0;
     d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
+    d.line_block = 128;
     d.dt = P.dt;
     d.nu = 2.0 / P.Re_inner;
     d.W_outer = P.Re_outer / P.Re_inner;
@@ -397,9 +441,16 @@ int init_handle(tc_handle* h) {
     int hf[4];
     CK(cudaMemcpy(hf, d.flag, sizeof(hf), cudaMemcpyDeviceToHost));
     if (hf[1]) { set_err("a radial system has a vanishing pivot (LU without pivoting)"); return TC_ERR_STATE; }
+    if (P.autotune) {
+        if ((rc_ = autotune(h))) return rc_;
+    }
     h->need_init = true;
     return TC_OK;
 }
+
+}  // namespace
+
+namespace tcx {
 
 int ensure_init(tc_handle* h) {
     if (!h->need_init) return TC_OK;
@@ -445,7 +496,26 @@ int validate(const tc_params* p) {
     return TC_OK;
 }
 
-}  // namespace
+// Sum of the allocations of init_handle (plus the physical-space buffer of
+// tc_get_field and a per-allocation rounding allowance of 2 MiB).
+size_t estimate_device_bytes(const tc_params& p) {
+    const size_t Nr = p.Nr, Nh = p.Ntheta / 2, Nz = p.Nz, Mt = 3 * (size_t)p.Ntheta / 2, Mz = 3 * Nz / 2;
+    const size_t np = Nz * Nh, P1 = Nr * np, Z1 = Nr * Mz * Nh;
+    size_t b = 0;
+    b += (6 + TC_NPROD) * P1 * sizeof(double2);                 // fields, products
+    b += (3 + TC_NPROD) * Z1 * sizeof(double2);                 // zbuf, pbuf
+    b += (3 + 3) * Nr * 5 * np * sizeof(double);                // LU tables
+    b += Nr * 5 * np * sizeof(double) + 2 * Nr * np * sizeof(double);   // L band, c, c1
+    b += Nr * Mz * Mt * sizeof(double);                         // physical output (on demand)
+    b += 64 * Nr * sizeof(double) + 4 * (Mz + 2 * Mt) * sizeof(double2);  // radial tables, twiddles
+    return b + 40 * (2u << 20);
+}
+
+}  // namespace tcx
+using tcx::ensure_init;
+using tcx::launch_step;
+using tcx::ensure_graph;
+using tcx::validate;
 
 extern "C" {
 
@@ -494,12 +564,17 @@ int tc_set_stream(tc_handle* h, void* s) {
     return TC_OK;
 }
 
-static int check_flags(tc_handle* h) {
+}  // extern "C"
+
+int tcx::check_flags(tc_handle* h) {
     int hf[4];
     CK(cudaMemcpy(hf, h->d.flag, sizeof(hf), cudaMemcpyDeviceToHost));
     if (hf[0]) { set_err("non-finite value in v or eta"); return TC_ERR_NONFINITE; }
     return TC_OK;
 }
+using tcx::check_flags;
+
+extern "C" {
 
 int tc_advance_substeps(tc_handle* h, int nsub) {
     if (!h || nsub < 0) { set_err("invalid handle or substep count"); return TC_ERR_ARG; }

@@ -26,6 +26,7 @@ struct TcDev {
     int npairs;                 // Nz * Nh
     int mixed;                  // 1: float32 FFT/products
     int ztile;                  // azimuthal columns per CTA of the z kernels (divides Nh)
+    int line_block;             // threads per block of the line kernel
     double dt, nu, m0, alpha0, W_outer;
     // RK coefficients of substep k and of the substep after it
     double rk_alpha[3], rk_beta[3], rk_gamma[3], rk_zeta[3];

@@ -336,7 +336,7 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 // formed in float32 from the float32 products; the continuity term, the
 // right sides, the solves, the RK memory and the reconstruction are float64.
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_line(TcDev d, int k) {
+__global__ void __launch_bounds__(256) k_line(TcDev d, int k) {
     typedef typename std::conditional<MIXED, float, double>::type T;
     typedef typename std::conditional<MIXED, float2, double2>::type CT;
     const int pair = blockIdx.x * blockDim.x + threadIdx.x;
@@ -765,8 +765,9 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
 }
 
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
-    if (d.mixed) k_line<true><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
-    else k_line<false><<<(d.npairs + 127) / 128, 128, 0, s>>>(d, k);
+    const int bs = d.line_block > 0 ? d.line_block : 128;
+    if (d.mixed) k_line<true><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
+    else k_line<false><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
 }
 
 static size_t mean_smem(const TcDev& d) { return (size_t)(2 * d.Nr * 5 * 2 + 2 * d.Nr * 3) * sizeof(double); }

@@ -43,3 +43,15 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.tc_get_field(None, 0, 0, None, 0) == tc.TC_ERR_ARG
     assert lib.tc_field_bytes(None, 0, 0) == 0
     lib.tc_destroy(None)
+
+
+def test_device_byte_estimate_on_host(lib):
+    small = tc.make_params(33, 16, 16, 0.883, 200.0, 0.0, 1e-3)
+    big = tc.make_params(257, 512, 512, 0.883, 3000.0, 0.0, 1e-3)
+    bad = tc.make_params(5, 16, 16, 0.883, 200.0, 0.0, 1e-3)
+    assert tc.tc_estimate_device_bytes(bad) == 0
+    b_small, b_big = tc.tc_estimate_device_bytes(small), tc.tc_estimate_device_bytes(big)
+    assert 0 < b_small < b_big
+    # the 257 x 512 x 512 case: 11 spectral fields, 8 plane buffers, 8.5 tables per point
+    P = 257 * 512 * 256
+    assert b_big > P * (11 * 16 + 8 * 16 * 1.5 + 37 * 8)
