@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--workload", default="tc-257x512x512")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -257,7 +257,7 @@ def run_gpu(args):
         from paper_0711_1429_gb300 import build as b
         b.build()
     w = WORKLOADS[args.workload]
-    prec = tc.TC_PREC_MIXED if args.precision == "mixed" else tc.TC_PREC_FP64
+    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[args.precision]
     Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
     gp = Nr * Nt * Nz
     m0, a0, rc = box_defaults(w["zeta"])
@@ -306,7 +306,7 @@ def run_gpu(args):
     a = alg[dom]
     t = ph[dom] * 1e-3
     if a["flops"] is not None:
-        pk = peaks["fp32_tflops"] if args.precision == "mixed" else peaks["fp64_tflops"]
+        pk = peaks["fp64_tflops"] if args.precision == "fp64" else peaks["fp32_tflops"]
         roof = {"bound": "alu", "achieved": a["flops"] / t / 1e12, "peak": pk, "unit": "TFLOP/s",
                 "frac": a["flops"] / t / 1e12 / pk, "traffic": None,
                 "kernel": dom, "peak_source": "measured FMA probe (tc_fma_peak) in this run",
@@ -350,7 +350,7 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "Nr": Nr, "Ntheta": Nt, "Nz": Nz,
                        "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
@@ -400,7 +400,7 @@ def run_batch(args):
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist = Dist(world, rank, "nccl")
-    prec = tc.TC_PREC_MIXED if args.precision == "mixed" else tc.TC_PREC_FP64
+    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[args.precision]
     rng = np.random.default_rng(1000 + rank)
     cases = [ensemble_case(rng, i, prec) for i in range(args.ncases)]
     for p, _ in cases:
@@ -434,7 +434,7 @@ def run_batch(args):
     line = {"metric": METRIC, "value": gp * args.steps * world / (total / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": f"batch{args.ncases}", "cases": args.ncases, "gridpoints": gp,
                        "precision": args.precision, "graph": "one CUDA graph per step, one branch per case",
@@ -453,7 +453,7 @@ def run_served(args):
     import paper_0711_1429_gb300 as tc
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    prec = tc.TC_PREC_MIXED if args.precision == "mixed" else tc.TC_PREC_FP64
+    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[args.precision]
     rng = np.random.default_rng(7 + rank)
     # Poisson arrivals over the window, cases as the ensemble plus 5% 257 x 256 x 256
     t, arrivals = 0.0, []
@@ -491,7 +491,7 @@ def run_served(args):
     line = {"metric": METRIC, "value": st["gridpoint_steps"] / (st["busy_ms"] / 1e3), "unit": UNIT,
             "n_gpus": 1, "steps": int(st["steps"]), "warmup": 0, "ms_per_step": st["busy_ms"] / max(1, nsteps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[args.precision], "data": "synthetic",
             "config": {"workload": "served", "requests": len(arrivals), "rate_per_s": args.serve_rate,
                        "window_s": args.serve_seconds, "budget_gb": args.budget_gb,
                        "precision": args.precision, "peak_active": st["peak_active"],

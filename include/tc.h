@@ -66,9 +66,12 @@ enum { TC_SPECTRAL = 0, TC_PHYSICAL = 1 };
 
 enum {
     TC_PREC_FP64 = 0,       /* every step in float64 */
-    TC_PREC_MIXED = 1       /* FFTs and products in float32; radial rows,
+    TC_PREC_MIXED = 1,      /* FFTs and products in float32; radial rows,
                                banded solves, continuity and the mean mode in
                                float64 */
+    TC_PREC_DF64 = 2        /* FFTs and products in double-float arithmetic
+                               (pairs of float32, ~48 significand bits) on the
+                               float32 pipe; everything else as TC_PREC_FP64 */
 };
 
 typedef struct {

@@ -18,7 +18,7 @@ HEADER = os.path.join(_HERE, "..", "include", "tc.h")
 TC_OK, TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_NONFINITE, TC_ERR_SIZE, TC_ERR_TIMEOUT, TC_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 TC_FIELD_U, TC_FIELD_V, TC_FIELD_W, TC_FIELD_ETA, TC_FIELD_MEAN_U, TC_FIELD_MEAN_W = range(6)
 TC_SPECTRAL, TC_PHYSICAL = 0, 1
-TC_PREC_FP64, TC_PREC_MIXED = 0, 1
+TC_PREC_FP64, TC_PREC_MIXED, TC_PREC_DF64 = 0, 1, 2
 
 
 class TcError(RuntimeError):

@@ -266,7 +266,7 @@ std::map<std::array<int, 4>, std::pair<int, int>> g_tune;
 
 int autotune(tc_handle* h) {
     TcDev& d = h->d;
-    const std::array<int, 4> key = {d.Nr, 2 * d.Nh, d.Nz, d.mixed};
+    const std::array<int, 4> key = {d.Nr, 2 * d.Nh, d.Nz, d.prec};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -323,6 +323,7 @@ int init_handle(tc_handle* h) {
     d.Mz = 3 * P.Nz / 2;
     d.npairs = d.Nz * d.Nh;
     d.mixed = P.precision == TC_PREC_MIXED ? 1 : 0;
+    d.prec = P.precision;
     d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
     d.line_block = 128;
     d.dt = P.dt;
@@ -386,6 +387,25 @@ int init_handle(tc_handle* h) {
         twr_f[k] = make_float2((float)cosl(a), (float)sinl(a));
     }
     if (twh_d.empty()) { twh_d.push_back(make_double2(1, 0)); twh_f.push_back(make_float2(1, 0)); }
+    {   // double-float tables: hi = nearest float, lo = nearest float of the rest
+        auto split = [](const std::vector<ld>& re, const std::vector<ld>& im, size_t n) {
+            std::vector<float4> o(n > 0 ? n : 1, make_float4(1.0f, 0.0f, 0.0f, 0.0f));
+            for (size_t i = 0; i < n; ++i) {
+                const float rh = (float)re[i], ih = (float)im[i];
+                o[i] = make_float4(rh, (float)(re[i] - (ld)rh), ih, (float)(im[i] - (ld)ih));
+            }
+            return o;
+        };
+        std::vector<ld> rr(d.Mt / 2), ri(d.Mt / 2);
+        for (int k = 0; k < d.Mt / 2; ++k) {
+            const ld a = -6.283185307179586476925286766559005768L * (ld)k / (ld)d.Mt;
+            rr[k] = cosl(a); ri[k] = sinl(a);
+        }
+        if ((rc_ = upload(h, d.twz_x, split(zr, zi, zr.size())))) return rc_;
+        if ((rc_ = upload(h, d.twt_x, split(tr, ti, tr.size())))) return rc_;
+        if ((rc_ = upload(h, d.twh_x, split(hr, hi, hr.size())))) return rc_;
+        if ((rc_ = upload(h, d.twr_x, split(rr, ri, rr.size())))) return rc_;
+    }
     if ((rc_ = upload(h, d.twh_d, twh_d))) return rc_;
     if ((rc_ = upload(h, d.twh_f, twh_f))) return rc_;
     if ((rc_ = upload(h, d.twr_d, twr_d))) return rc_;
@@ -492,7 +512,7 @@ int validate(const tc_params* p) {
     if (!(p->radius_ratio > 0.0 && p->radius_ratio < 1.0)) { set_err("radius ratio must lie in (0, 1)"); return TC_ERR_ARG; }
     if (!(p->Re_inner > 0.0) || !std::isfinite(p->Re_outer)) { set_err("Re_inner must be > 0 and Re_outer finite"); return TC_ERR_ARG; }
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { set_err("dt must be > 0"); return TC_ERR_ARG; }
-    if (p->precision != TC_PREC_FP64 && p->precision != TC_PREC_MIXED) { set_err("unknown precision"); return TC_ERR_ARG; }
+    if (p->precision != TC_PREC_FP64 && p->precision != TC_PREC_MIXED && p->precision != TC_PREC_DF64) { set_err("unknown precision"); return TC_ERR_ARG; }
     return TC_OK;
 }
 

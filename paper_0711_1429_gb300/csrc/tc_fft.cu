@@ -21,10 +21,13 @@
 // Template parameter T is the arithmetic type (double, or float in the
 // mixed-precision form).
 #include "tc_internal.h"
+#include "tc_dfloat.h"
+#include <type_traits>
 
 template <typename T> struct V2;
 template <> struct V2<double> { typedef double2 t; };
 template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<dfloat> { typedef dcomplex t; };
 
 template <typename C> __device__ __forceinline__ C c_add(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
@@ -34,6 +37,19 @@ template <int SIGN, typename C> __device__ __forceinline__ C c_tw(C a, C w) {
     C r;
     if (SIGN < 0) { r.x = a.x * w.x - a.y * w.y; r.y = a.x * w.y + a.y * w.x; }
     else          { r.x = a.x * w.x + a.y * w.y; r.y = a.y * w.x - a.x * w.y; }
+    return r;
+}
+// double-float complex products: one renormalisation per component
+template <> __device__ __forceinline__ dcomplex c_tw<-1, dcomplex>(dcomplex a, dcomplex w) {
+    dcomplex r;
+    r.x = df_dot2(a.x, w.x, a.y, w.y, -1.0f);
+    r.y = df_dot2(a.x, w.y, a.y, w.x, 1.0f);
+    return r;
+}
+template <> __device__ __forceinline__ dcomplex c_tw<1, dcomplex>(dcomplex a, dcomplex w) {
+    dcomplex r;
+    r.x = df_dot2(a.x, w.x, a.y, w.y, 1.0f);
+    r.y = df_dot2(a.y, w.x, a.x, w.y, -1.0f);
     return r;
 }
 // multiply by SIGN * i
@@ -104,16 +120,118 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
     return src;
 }
 
+// ---- compile-time plans ------------------------------------------------------
+// The same mixed-radix plan (radix-3 stages, then 4, then 2; twiddle offsets
+// as on the host) with the length known at compile time: every division by
+// the stage constants becomes a multiply-shift and the stage loop unrolls.
+__host__ __device__ constexpr int plan_nst(int M) {
+    int n = 0;
+    while (M % 3 == 0) { M /= 3; ++n; }
+    while (M % 4 == 0) { M /= 4; ++n; }
+    while (M % 2 == 0) { M /= 2; ++n; }
+    return n;
+}
+__host__ __device__ constexpr int plan_radix(int M, int s) {
+    int i = 0;
+    while (M % 3 == 0) { if (i == s) return 3; M /= 3; ++i; }
+    while (M % 4 == 0) { if (i == s) return 4; M /= 4; ++i; }
+    while (M % 2 == 0) { if (i == s) return 2; M /= 2; ++i; }
+    return 1;
+}
+__host__ __device__ constexpr int plan_ns(int M, int s) {
+    int ns = 1;
+    for (int i = 0; i < s; ++i) ns *= plan_radix(M, i);
+    return ns;
+}
+__host__ __device__ constexpr int plan_off(int M, int s) {
+    int o = 0;
+    for (int i = 0; i < s; ++i) o += plan_ns(M, i) * (plan_radix(M, i) - 1);
+    return o;
+}
+
+template <typename T, int SIGN, int M, int S>
+__device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t* src, typename V2<T>::t* dst,
+                                                              int ncols, const typename V2<T>::t* __restrict__ tw) {
+    typedef typename V2<T>::t C;
+    if constexpr (S == plan_nst(M)) {
+        return src;
+    } else {
+        constexpr int R = plan_radix(M, S);
+        constexpr int Ns = plan_ns(M, S);
+        constexpr int nb = M / R;
+        const C* tws = tw + plan_off(M, S);
+        for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
+            const int col = b / nb;
+            const int j = b - col * nb;
+            const int jm = j % Ns;
+            const C* sc = src + col * M;
+            C* dc = dst + col * M + (j / Ns) * Ns * R + jm;
+            if constexpr (R == 4) {
+                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb], v3 = sc[j + 3 * nb];
+                if constexpr (Ns > 1) {
+                    const C* t = tws + jm * 3;
+                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]); v3 = c_tw<SIGN>(v3, t[2]);
+                }
+                C a0 = c_add(v0, v2), a1 = c_sub(v0, v2), a2 = c_add(v1, v3), a3 = c_si<SIGN>(c_sub(v1, v3));
+                dc[0] = c_add(a0, a2);
+                dc[Ns] = c_add(a1, a3);
+                dc[2 * Ns] = c_sub(a0, a2);
+                dc[3 * Ns] = c_sub(a1, a3);
+            } else if constexpr (R == 3) {
+                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb];
+                if constexpr (Ns > 1) {
+                    const C* t = tws + jm * 2;
+                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]);
+                }
+                const T h = (T)0.5;
+                const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
+                C sm = c_add(v1, v2), df = c_sub(v1, v2);
+                C t0; t0.x = v0.x - h * sm.x; t0.y = v0.y - h * sm.y;
+                C id = c_si<SIGN>(df); id.x *= s3; id.y *= s3;
+                dc[0] = c_add(v0, sm);
+                dc[Ns] = c_add(t0, id);
+                dc[2 * Ns] = c_sub(t0, id);
+            } else {
+                C v0 = sc[j], v1 = sc[j + nb];
+                if constexpr (Ns > 1) v1 = c_tw<SIGN>(v1, tws[jm]);
+                dc[0] = c_add(v0, v1);
+                dc[Ns] = c_sub(v0, v1);
+            }
+        }
+        __syncthreads();
+        return fft_fixed_stage<T, SIGN, M, S + 1>(dst, src, ncols, tw);
+    }
+}
+
+// Dispatch on the transform length: compile-time plans for the lengths of
+// the supported grids, the run-time plan otherwise (same arithmetic).
+template <typename T, int SIGN>
+__device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
+                                  const FftPlan& pl, const typename V2<T>::t* __restrict__ tw) {
+#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, 0>(buf0, buf1, ncols, tw);
+    switch (pl.M) {
+        TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
+        TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
+        TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
+        default: return fft_stockham<T, SIGN>(buf0, buf1, ncols, pl, tw);
+    }
+#undef TC_FFT_CASE
+}
+
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twz(const TcDev& d);
+template <> __device__ __forceinline__ const dcomplex* twz<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twz_x); }
 template <> __device__ __forceinline__ const double2* twz<double>(const TcDev& d) { return d.twz_d; }
 template <> __device__ __forceinline__ const float2* twz<float>(const TcDev& d) { return d.twz_f; }
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twt(const TcDev& d);
+template <> __device__ __forceinline__ const dcomplex* twt<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twt_x); }
 template <> __device__ __forceinline__ const double2* twt<double>(const TcDev& d) { return d.twt_d; }
 template <> __device__ __forceinline__ const float2* twt<float>(const TcDev& d) { return d.twt_f; }
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twh(const TcDev& d);
+template <> __device__ __forceinline__ const dcomplex* twh<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twh_x); }
 template <> __device__ __forceinline__ const double2* twh<double>(const TcDev& d) { return d.twh_d; }
 template <> __device__ __forceinline__ const float2* twh<float>(const TcDev& d) { return d.twh_f; }
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twr(const TcDev& d);
+template <> __device__ __forceinline__ const dcomplex* twr<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twr_x); }
 template <> __device__ __forceinline__ const double2* twr<double>(const TcDev& d) { return d.twr_d; }
 template <> __device__ __forceinline__ const float2* twr<float>(const TcDev& d) { return d.twr_f; }
 
@@ -146,7 +264,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft_stockham<T, +1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, +1>(buf0, buf1, ct, d.pz, twz<T>(d));
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
@@ -210,8 +328,8 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         hA[k] = z;
     }
     __syncthreads();
-    C* r1 = fft_stockham<T, +1>(fA, fB, 1, d.pt, twt<T>(d));
-    C* r2 = fft_stockham<T, +1>(hA, hB, 1, d.ph, twh<T>(d));
+    C* r1 = fft<T, +1>(fA, fB, 1, d.pt, twt<T>(d));
+    C* r2 = fft<T, +1>(hA, hB, 1, d.ph, twh<T>(d));
     C* o1 = (r1 == fA) ? fB : fA;
     C* o2 = (r2 == hA) ? hB : hA;
     for (int m = threadIdx.x; m < H; m += blockDim.x) {
@@ -231,8 +349,8 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         o2[m] = z;
     }
     __syncthreads();
-    C* out = fft_stockham<T, -1>(o1, r1, 2, d.pt, twt<T>(d));
-    C* out2 = fft_stockham<T, -1>(o2, r2, 1, d.ph, twh<T>(d));
+    C* out = fft<T, -1>(o1, r1, 2, d.pt, twt<T>(d));
+    C* out2 = fft<T, -1>(o2, r2, 1, d.ph, twh<T>(d));
     C* pb = reinterpret_cast<C*>(d.pbuf);
     for (int idx = threadIdx.x; idx < 3 * Nh; idx += blockDim.x) {
         const int c = idx / Nh, j = idx - c * Nh;
@@ -277,9 +395,11 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
-    C* res = fft_stockham<T, -1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, -1>(buf0, buf1, ct, d.pz, twz<T>(d));
     const T scale = (T)(1.0 / ((double)d.Mt * (double)d.Mz));
-    C* outp = reinterpret_cast<C*>(d.prod) + ((size_t)p * Nr + r) * Nz * Nh;
+    // products: double2 for float64 and double-float, float2 for the mixed form
+    typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type PO;
+    PO* outp = reinterpret_cast<PO*>(d.prod) + ((size_t)p * Nr + r) * Nz * Nh;
     for (int idx = threadIdx.x; idx < ct * Nz; idx += blockDim.x) {
         const int s = idx / ct, c = idx - s * ct;
         C val; val.x = 0; val.y = 0;
@@ -289,7 +409,10 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
             val = res[c * Mz + qq];
             val.x *= scale; val.y *= scale;
         }
-        outp[(size_t)s * Nh + j0 + c] = val;
+        PO o;
+        o.x = (decltype(o.x))val.x;
+        o.y = (decltype(o.y))val.y;
+        outp[(size_t)s * Nh + j0 + c] = o;
     }
 }
 
@@ -348,7 +471,8 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
 }
 
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s) {
-    if (d.mixed) plane_kernel_t<float>(d, which, s);
+    if (d.prec == 1) plane_kernel_t<float>(d, which, s);
+    else if (d.prec == 2) plane_kernel_t<dfloat>(d, which, s);
     else plane_kernel_t<double>(d, which, s);
 }
 
@@ -377,6 +501,7 @@ cudaError_t tc_set_kernel_attributes() {
     set((const void*)k_zinv<double>); set((const void*)k_zinv<float>);
     set((const void*)k_rows<double>); set((const void*)k_rows<float>);
     set((const void*)k_zfwd<double>); set((const void*)k_zfwd<float>);
+    set((const void*)k_zinv<dfloat>); set((const void*)k_rows<dfloat>); set((const void*)k_zfwd<dfloat>);
     set((const void*)k_rows_phys);
     return e;
 }

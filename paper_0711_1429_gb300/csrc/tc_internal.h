@@ -24,7 +24,8 @@ struct FftPlan {
 struct TcDev {
     int Nr, Nz, Nh, Mt, Mz;
     int npairs;                 // Nz * Nh
-    int mixed;                  // 1: float32 FFT/products
+    int mixed;                  // 1: float32 FFT/products (precision == TC_PREC_MIXED)
+    int prec;                   // TC_PREC_FP64, TC_PREC_MIXED or TC_PREC_DF64
     int ztile;                  // azimuthal columns per CTA of the z kernels (divides Nh)
     int line_block;             // threads per block of the line kernel
     double dt, nu, m0, alpha0, W_outer;
@@ -79,6 +80,12 @@ struct TcDev {
     const float2* twt_f;
     const float2* twh_f;
     const float2* twr_f;
+    // double-float copies (hi, lo float pairs) for TC_PREC_DF64, layout
+    // {re.hi, re.lo, im.hi, im.lo}
+    const float4* twz_x;
+    const float4* twt_x;
+    const float4* twh_x;
+    const float4* twr_x;
 
     // physical output buffer for tc_get_field (float64 [Nr][Mz][Mt])
     double* phys;

@@ -272,3 +272,29 @@ def test_full_size_first_substep_sampled_pairs():
         err = relerr(G[:, sel[0], sel[1]], O[:, sel[0], sel[1]])
         assert err < 1e-10, (key, err)
     assert relerr(g["U"], sub.U) < 1e-10 and relerr(g["W"], sub.W) < 1e-10
+
+
+@pytest.mark.parametrize("steps,tol", [(1, 1e-10), (50, 1e-8)])
+def test_df64_form_meets_fp64_tolerances_small(steps, tol):
+    """Double-float FFTs and products (float32 pairs) hold the FP64 parity bar."""
+    v, e = workload_inputs("tc-small-33x16x16")
+    c, s, h = _pair(SMALL, v, e, precision=tc.TC_PREC_DF64)
+    try:
+        tc.tc_step(h, steps)
+        s.step(steps)
+        err = _check(c, s, h, tol)
+        assert max(err.values()) > 0.0
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_df64_form_one_step_129():
+    cfg = dict(Nr=129, Ntheta=128, Nz=128, zeta=0.883, Re_i=3000.0, Re_o=0.0, dt=1e-3)
+    v, e = workload_inputs("tc-129x128x128")
+    c, s, h = _pair(cfg, v, e, precision=tc.TC_PREC_DF64)
+    try:
+        tc.tc_step(h, 1)
+        s.step(1)
+        _check(c, s, h, 1e-10)
+    finally:
+        tc.tc_destroy(h)
