@@ -367,6 +367,18 @@ int init_handle(tc_handle* h) {
         if ((rc_ = upload(h, d.l1f, f1))) return rc_;
         if ((rc_ = upload(h, d.l2f, f2))) return rc_;
         if ((rc_ = upload(h, d.rinvf, fr))) return rc_;
+        auto dsplit = [](const std::vector<double>& v) {
+            std::vector<float2> o(v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const float hh = (float)v[i];
+                o[i] = make_float2(hh, (float)(v[i] - (double)hh));
+            }
+            return o;
+        };
+        if ((rc_ = upload(h, d.d0x, dsplit(h->S.d0)))) return rc_;
+        if ((rc_ = upload(h, d.l1x, dsplit(h->S.l1)))) return rc_;
+        if ((rc_ = upload(h, d.l2x, dsplit(h->S.l2)))) return rc_;
+        if ((rc_ = upload(h, d.rinvx, dsplit(rinv)))) return rc_;
     }
     // FFT plans
     std::vector<ld> zr, zi, tr, ti, hr, hi;
@@ -450,6 +462,10 @@ int init_handle(tc_handle* h) {
     if ((rc_ = dalloc(h, d.tab_lv, (size_t)d.Nr * 5 * d.npairs))) return rc_;
     if ((rc_ = dalloc(h, d.tab_c, (size_t)d.Nr * d.npairs))) return rc_;
     if ((rc_ = dalloc(h, d.tab_c1, (size_t)d.Nr * d.npairs))) return rc_;
+    if (d.prec == TC_PREC_DF64) {
+        if ((rc_ = dalloc(h, d.tab_cx, (size_t)d.Nr * d.npairs))) return rc_;
+        if ((rc_ = dalloc(h, d.tab_c1x, (size_t)d.Nr * d.npairs))) return rc_;
+    }
     int* flag;
     if ((rc_ = dalloc(h, flag, 4))) return rc_;
     CK(cudaMemset(flag, 0, 4 * sizeof(int)));
@@ -525,7 +541,7 @@ size_t estimate_device_bytes(const tc_params& p) {
     b += (6 + TC_NPROD) * P1 * sizeof(double2);                 // fields, products
     b += (3 + TC_NPROD) * Z1 * sizeof(double2);                 // zbuf, pbuf
     b += (3 + 3) * Nr * 5 * np * sizeof(double);                // LU tables
-    b += Nr * 5 * np * sizeof(double) + 2 * Nr * np * sizeof(double);   // L band, c, c1
+    b += Nr * 5 * np * sizeof(double) + 4 * Nr * np * sizeof(double);   // L band, c, c1 (+ double-float copies)
     b += Nr * Mz * Mt * sizeof(double);                         // physical output (on demand)
     b += 64 * Nr * sizeof(double) + 4 * (Mz + 2 * Mt) * sizeof(double2);  // radial tables, twiddles
     return b + 40 * (2u << 20);

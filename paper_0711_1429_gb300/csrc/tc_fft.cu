@@ -397,8 +397,9 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
     __syncthreads();
     C* res = fft<T, -1>(buf0, buf1, ct, d.pz, twz<T>(d));
     const T scale = (T)(1.0 / ((double)d.Mt * (double)d.Mz));
-    // products: double2 for float64 and double-float, float2 for the mixed form
-    typedef typename std::conditional<std::is_same<T, float>::value, float2, double2>::type PO;
+    // products: double2 for float64, float2 for the mixed form, double-float
+    // pairs for the double-float form (read as such by the line kernel)
+    typedef typename std::conditional<std::is_same<T, double>::value, double2, C>::type PO;
     PO* outp = reinterpret_cast<PO*>(d.prod) + ((size_t)p * Nr + r) * Nz * Nh;
     for (int idx = threadIdx.x; idx < ct * Nz; idx += blockDim.x) {
         const int s = idx / ct, c = idx - s * ct;
@@ -409,10 +410,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
             val = res[c * Mz + qq];
             val.x *= scale; val.y *= scale;
         }
-        PO o;
-        o.x = (decltype(o.x))val.x;
-        o.y = (decltype(o.y))val.y;
-        outp[(size_t)s * Nh + j0 + c] = o;
+        outp[(size_t)s * Nh + j0 + c] = val;
     }
 }
 

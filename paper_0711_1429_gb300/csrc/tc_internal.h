@@ -59,6 +59,10 @@ struct TcDev {
     const float* l1f;
     const float* l2f;
     const float* rinvf;
+    const float2* d0x;          // double-float (hi, lo) copies of d0, l1, l2, 1/r
+    const float2* l1x;
+    const float2* l2x;
+    const float2* rinvx;
     const double* mean_lu;      // [2 profiles][3 substeps][Nr][5] + precombination
     const double* mean_L;       // [2][Nr][5] implicit bands of U and W rows
     // per-pair tables, structure of arrays [..][Nr][5][npairs]
@@ -67,6 +71,8 @@ struct TcDev {
     double* tab_lv;             // [Nr][5][npairs]
     double* tab_c;              // [Nr][npairs] c = 1/k^2
     double* tab_c1;             // [Nr][npairs] c1 = dc/dr
+    float2* tab_cx;             // double-float copies of c, c1 (TC_PREC_DF64 only)
+    float2* tab_c1x;
 
     // FFT plans and twiddles (double and float copies): pz (length Mz), pt
     // (Mt), ph (Mt/2, the real transforms of one signal) and twr[k] =

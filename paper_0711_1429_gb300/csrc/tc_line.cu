@@ -18,7 +18,10 @@
 // and prepares H_(k+1) = RHS_k + zeta_(k+1) dt E(x^(k-1)) + (beta_k +
 // alpha_(k+1)) dt L x^k, using M x^k = RHS_k + beta_k dt L x^k.
 #include "tc_internal.h"
+#include "tc_dfloat.h"
 #include <type_traits>
+
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return a * b + c; }
 
 namespace {
 
@@ -63,9 +66,20 @@ template <typename CT, typename T> __device__ __forceinline__ CT taxpy(CT a, T s
 template <typename CT, typename T> __device__ __forceinline__ CT tscale(T s, CT a) { CT r; r.x = s * a.x; r.y = s * a.y; return r; }
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d2(dcomplex a) { return make_double2((double)a.x, (double)a.y); }
 template <typename CT> __device__ __forceinline__ CT from_d2(double2 a);
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ dcomplex from_d2<dcomplex>(double2 a) { dcomplex r; r.x = dfloat(a.x); r.y = dfloat(a.y); return r; }
+__device__ __forceinline__ double2 ld_prod(const dcomplex* p, size_t o) { return to_d2(p[o]); }
+__device__ __forceinline__ dfloat as_df(float2 v) { return dfloat(v.x, v.y); }
+
+// element types of the three forms: 0 float64, 1 mixed (float32 explicit
+// rows), 2 double-float explicit rows
+template <int MODE> struct LineTypes;
+template <> struct LineTypes<0> { typedef double T; typedef double2 CT; };
+template <> struct LineTypes<1> { typedef float T; typedef float2 CT; };
+template <> struct LineTypes<2> { typedef dfloat T; typedef dcomplex CT; };
 
 // Pair index -> (n slot, j); returns false for pairs that are not evolved:
 // the axial Nyquist slot, (0,0) (mean flow) and (0, n<0) (conjugates).
@@ -161,6 +175,11 @@ __global__ void __launch_bounds__(128) k_setup(TcDev d) {
         const Coef q = coef_at(d.r[i], d.rinv[i], m, al);
         d.tab_c[(size_t)i * d.npairs + pair] = q.c;
         d.tab_c1[(size_t)i * d.npairs + pair] = q.c1;
+        if (d.tab_cx) {
+            const dfloat a(q.c), b(q.c1);
+            d.tab_cx[(size_t)i * d.npairs + pair] = make_float2(a.hi, a.lo);
+            d.tab_c1x[(size_t)i * d.npairs + pair] = make_float2(b.hi, b.lo);
+        }
     }
     // implicit band of the v rows (substep independent)
     for (int j = 2; j <= N - 3; ++j) {
@@ -333,12 +352,15 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 //        B = -i m uv/r + i alpha vw + 2 i nu m u/r^2
 // (the terms of Eqs. 6-7 regrouped per stencil; the vv parts cancel because
 // c k^2 = 1).  In the mixed form everything except the continuity term is
-// formed in float32 from the float32 products; the continuity term, the
-// right sides, the solves, the RK memory and the reconstruction are float64.
-template <bool MIXED>
+// formed in float32 from the float32 products; in the double-float form all
+// explicit rows are formed in double-float arithmetic (float32 pipe) from the
+// double-float products; the right sides, the solves, the RK memory and the
+// reconstruction are float64 in every form.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_line(TcDev d, int k) {
-    typedef typename std::conditional<MIXED, float, double>::type T;
-    typedef typename std::conditional<MIXED, float2, double2>::type CT;
+    constexpr bool MIXED = (MODE == 1);
+    typedef typename LineTypes<MODE>::T T;
+    typedef typename LineTypes<MODE>::CT CT;
     const int pair = blockIdx.x * blockDim.x + threadIdx.x;
     if (pair >= d.npairs) return;
     double m, al;
@@ -357,8 +379,12 @@ __global__ void __launch_bounds__(256) k_line(TcDev d, int k) {
     const T* w0s;
     const T* w1s;
     const T* w2s;
-    if constexpr (MIXED) { w0s = d.d0f; w1s = d.l1f; w2s = d.l2f; }
-    else { w0s = d.d0; w1s = d.l1; w2s = d.l2; }
+    if constexpr (MODE == 1) { w0s = d.d0f; w1s = d.l1f; w2s = d.l2f; }
+    else if constexpr (MODE == 2) {
+        w0s = reinterpret_cast<const dfloat*>(d.d0x);
+        w1s = reinterpret_cast<const dfloat*>(d.l1x);
+        w2s = reinterpret_cast<const dfloat*>(d.l2x);
+    } else { w0s = d.d0; w1s = d.l1; w2s = d.l2; }
 
     // ---- forward sweep: explicit rows, right sides, forward elimination ----
     CT Av[5], Bv[5], Cv[5], Ae[5], Be[5];
@@ -431,10 +457,11 @@ __global__ void __launch_bounds__(256) k_line(TcDev d, int k) {
             const CT pa = prod[o], uv = prod[o + PS], uw = prod[o + 2 * PS], vw = prod[o + 3 * PS], pb = prod[o + 4 * PS];
             const double2 Ud = d.u[o], Vd = d.v[o], Wd = d.w[o];
             const CT U = from_d2<CT>(Ud), V = from_d2<CT>(Vd), W = from_d2<CT>(Wd);
-            const double cd = d.tab_c[o], c1d = d.tab_c1[o];
             T ri, c, c1;
-            if constexpr (MIXED) { ri = d.rinvf[i]; c = (T)cd; c1 = (T)c1d; }
-            else { ri = d.rinv[i]; c = cd; c1 = c1d; }
+            double c1d = 0.0;
+            if constexpr (MODE == 1) { ri = d.rinvf[i]; c = (T)d.tab_c[o]; c1d = d.tab_c1[o]; c1 = (T)c1d; }
+            else if constexpr (MODE == 2) { ri = as_df(d.rinvx[i]); c = as_df(d.tab_cx[o]); c1 = as_df(d.tab_c1x[o]); }
+            else { ri = d.rinv[i]; c = d.tab_c[o]; c1d = d.tab_c1[o]; c1 = c1d; }
             const T ri2 = ri * ri;
             // v rows
             CT a = timag(-at, uv);
@@ -450,9 +477,16 @@ __global__ void __launch_bounds__(256) k_line(TcDev d, int k) {
             CT cc = timag(-at * c, uv);
             cc = tadd(cc, timag(-mt * c * ri, vw));
             cc = tadd(cc, timag((T)2 * nut * mt * c * ri2, W));
-            const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
-            if constexpr (MIXED) Cp[4] = cscale(c1d, phi);
-            else cc = caxpy(cc, -3.0 * nu * c1d, phi);
+            if constexpr (MODE == 1) {
+                const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
+                Cp[4] = cscale(c1d, phi);
+            } else if constexpr (MODE == 2) {
+                const CT phi = tadd(timag(at, U), timag(mt * ri, W));
+                cc = taxpy(cc, (T)(-3.0 * nu) * c1, phi);
+            } else {
+                const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
+                cc = caxpy(cc, -3.0 * nu * c1d, phi);
+            }
             Av[4] = a; Bv[4] = b; Cv[4] = cc;
             // eta rows
             CT ae = tscale(mt * at * ri, pa);
@@ -766,20 +800,24 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
 
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
     const int bs = d.line_block > 0 ? d.line_block : 128;
-    if (d.mixed) k_line<true><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
-    else k_line<false><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
+    if (d.prec == 1) k_line<1><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
+    else if (d.prec == 2) k_line<2><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
+    else k_line<0><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
 }
 
 static size_t mean_smem(const TcDev& d) { return (size_t)(2 * d.Nr * 5 * 2 + 2 * d.Nr * 3) * sizeof(double); }
 
 void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s) {
-    if (d.mixed) k_mean<float2><<<1, 256, mean_smem(d), s>>>(d, k, 0);
+    if (d.prec == 1) k_mean<float2><<<1, 256, mean_smem(d), s>>>(d, k, 0);
+    else if (d.prec == 2) k_mean<dcomplex><<<1, 256, mean_smem(d), s>>>(d, k, 0);
     else k_mean<double2><<<1, 256, mean_smem(d), s>>>(d, k, 0);
 }
 
 cudaError_t tc_set_line_kernel_attributes() {
     const int lim = 200 * 1024;
     cudaError_t e = cudaFuncSetAttribute((const void*)k_mean<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void*)k_mean<dcomplex>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void*)k_mean<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
