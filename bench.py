@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--sample-planes", type=int, default=4)
     p.add_argument("--sample-pairs", type=int, default=1024)
@@ -244,6 +245,68 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False):
+    """Create the case in one precision form, warm up, time K steps with CUDA
+    events on the launch stream, then time each kernel (tc_phase_times)."""
+    Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
+    h = tc.tc_create_ex(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], precision=prec, device=local)
+    stream = torch.cuda.current_stream()
+    tc.tc_set_stream(h, stream.cuda_stream)
+    tc.tc_set_field(h, tc.TC_FIELD_V, v)
+    tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
+    tc.tc_step(h, max(args.warmup, 3))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if measure_clocks else None
+    dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        tc.tc_step(h, 1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop() if clocks else None
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
+    total_ms = dist.max(ev[0].elapsed_time(ev[args.steps]))
+    state = {"v": tc.tc_get_field(h, tc.TC_FIELD_V), "eta": tc.tc_get_field(h, tc.TC_FIELD_ETA),
+             "W": tc.tc_get_field(h, tc.TC_FIELD_MEAN_W), "U": tc.tc_get_field(h, tc.TC_FIELD_MEAN_U)}
+    torque = tc.tc_torque_stats(h)
+    ph = tc.tc_phase_times(h, 1)
+    return h, {"total_ms": total_ms, "per": per, "clk": clk, "state": state, "phase_ms": ph,
+               "torque": torque}
+
+
+def roofline_of(w, prec_name, ph, peaks):
+    alg = algorithmic(w, prec_name)
+    dom = max(ph, key=ph.get)
+    meas_peaks = {}
+    try:
+        meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = meas_peaks.get("hbm_gbs")
+    a = alg[dom]
+    t = ph[dom] * 1e-3
+    if a["flops"] is not None:
+        pk = peaks["fp64_tflops"] if prec_name == "fp64" else peaks["fp32_tflops"]
+        roof = {"bound": "alu", "achieved": a["flops"] / t / 1e12, "peak": pk, "unit": "TFLOP/s",
+                "frac": a["flops"] / t / 1e12 / pk, "traffic": None, "kernel": dom,
+                "peak_source": ("measured FP64 FMA probe (tc_fma_peak) in this run" if prec_name == "fp64"
+                                else "measured FP32 FMA probe (tc_fma_peak) in this run"),
+                "hbm_gbs_of_kernel": a["bytes"] / t / 1e9}
+    else:
+        roof = {"bound": "hbm", "achieved": a["bytes"] / t / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": (a["bytes"] / t / 1e9 / hbm) if hbm else None, "traffic": None,
+                "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)",
+                "note": "the line kernel is float64-issue-bound (ncu); bytes/time is reported against HBM"}
+    roof["phase_ms"] = ph
+    return roof
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -257,65 +320,20 @@ def run_gpu(args):
         from paper_0711_1429_gb300 import build as b
         b.build()
     w = WORKLOADS[args.workload]
-    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[args.precision]
+    PREC = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}
+    DTYPE = {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}
     Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
     gp = Nr * Nt * Nz
     m0, a0, rc = box_defaults(w["zeta"])
     v, e = initial_perturbation(Nr, Nt, Nz, w["seed"] + rank, w["spectrum"], w["amp"], m0=m0, alpha0=a0, rc=rc)
-    h = tc.tc_create_ex(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], precision=prec, device=local)
-    stream = torch.cuda.current_stream()
-    tc.tc_set_stream(h, stream.cuda_stream)
-    tc.tc_set_field(h, tc.TC_FIELD_V, v)
-    tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
     peaks = tc.tc_fma_peak(local)
-    tc.tc_step(h, max(args.warmup, 3))
-    torch.cuda.synchronize()
 
-    # ---- timed region: K steps, device time by CUDA events on the launch stream
-    clocks = ClockSampler(local)
-    dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    for i in range(args.steps):
-        tc.tc_step(h, 1)
-        ev[i + 1].record(stream)
-    torch.cuda.synchronize()
-    dist.barrier()
-    clk = clocks.stop()
-    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
-    total_ms = dist.max(total_ms)
-    value = gp * args.steps * world / (total_ms / 1e3)
-    qs = sorted(per)
-    p50 = statistics.median(qs)
-    p99 = qs[min(len(qs) - 1, int(round(0.99 * (len(qs) - 1))))]
-
-    # ---- per-kernel durations (events between kernels, unrolled steps)
-    ph = tc.tc_phase_times(h, 1)
-    alg = algorithmic(w, args.precision)
-    dom = max(ph, key=ph.get)
-    meas_peaks = {}
-    try:
-        meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = meas_peaks.get("hbm_gbs")
-    a = alg[dom]
-    t = ph[dom] * 1e-3
-    if a["flops"] is not None:
-        pk = peaks["fp64_tflops"] if args.precision == "fp64" else peaks["fp32_tflops"]
-        roof = {"bound": "alu", "achieved": a["flops"] / t / 1e12, "peak": pk, "unit": "TFLOP/s",
-                "frac": a["flops"] / t / 1e12 / pk, "traffic": None,
-                "kernel": dom, "peak_source": "measured FMA probe (tc_fma_peak) in this run",
-                "hbm_gbs_of_kernel": a["bytes"] / t / 1e9}
-    else:
-        roof = {"bound": "hbm", "achieved": a["bytes"] / t / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": (a["bytes"] / t / 1e9 / hbm) if hbm else None, "traffic": None,
-                "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)"}
-    roof["phase_ms"] = ph
+    h, main = time_form(tc, torch, w, PREC[args.precision], v, e, args, local, dist, measure_clocks=True)
+    value = gp * args.steps * world / (main["total_ms"] / 1e3)
+    per = main["per"]
+    p50 = statistics.median(per)
+    p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
+    roof = roofline_of(w, args.precision, main["phase_ms"], peaks)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -337,6 +355,27 @@ def run_gpu(args):
         e2e = {"value": gp * args.e2e_steps * world / wall, "unit": UNIT,
                "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + 7 * 8,
                "steps": args.e2e_steps, "torque_inner": stats["G_inner"]}
+    device_bytes = tc.tc_device_bytes(h)
+    tc.tc_destroy(h)
+
+    # ---- the other precision forms, same input and step count; error against this run
+    forms = {}
+    if not args.no_forms:
+        ref = main["state"]
+        for name in [p for p in ("df64", "mixed", "fp64") if p != args.precision]:
+            hf, res = time_form(tc, torch, w, PREC[name], v, e, args, local, dist)
+            tc.tc_destroy(hf)
+            err = {k: float(np.linalg.norm(res["state"][k] - ref[k]) / np.linalg.norm(ref[k]))
+                   for k in ("v", "eta", "W")}
+            err["U"] = float(np.linalg.norm(res["state"]["U"] - ref["U"]) / max(np.linalg.norm(ref["U"]), 1e-300))
+            err["torque_inner"] = abs(res["torque"]["G_inner"] - main["torque"]["G_inner"]) / main["torque"]["G_inner"]
+            rper = res["per"]
+            forms[name] = {"value": gp * args.steps * world / (res["total_ms"] / 1e3), "unit": UNIT,
+                           "ms_per_step": res["total_ms"] / args.steps, "dtype": DTYPE[name],
+                           "latency_ms": {"p50": statistics.median(rper),
+                                          "p99": rper[min(len(rper) - 1, int(round(0.99 * (len(rper) - 1))))]},
+                           "rel_l2_error_vs_" + args.precision: err,
+                           "roofline": roofline_of(w, name, res["phase_ms"], peaks)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -348,20 +387,17 @@ def run_gpu(args):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[-300:]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": main["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[args.precision],
-            "data": "synthetic",
+            "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": args.workload, "Nr": Nr, "Ntheta": Nt, "Nz": Nz,
                        "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
                        "precision": args.precision, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (state ~24 GB)",
-                       "device_bytes": tc.tc_device_bytes(h)},
+                       "l2": "inputs larger than L2 (state ~24 GB)", "device_bytes": device_bytes},
             "latency_ms": {"p50": p50, "p99": p99},
             "gpu_launches": 15 * args.steps,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "alu_peaks_tflops": peaks}
-    tc.tc_destroy(h)
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clk"],
+            "alu_peaks_tflops": peaks, "forms": forms}
     if rank == 0:
         print(json.dumps(line))
     dist.close()
