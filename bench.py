@@ -249,7 +249,8 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False)
     """Create the case in one precision form, warm up, time K steps with CUDA
     events on the launch stream, then time each kernel (tc_phase_times)."""
     Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
-    h = tc.tc_create_ex(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], precision=prec, device=local)
+    h = tc.tc_create_ex(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], precision=prec, device=local,
+                        autotune=1)
     stream = torch.cuda.current_stream()
     tc.tc_set_stream(h, stream.cuda_stream)
     tc.tc_set_field(h, tc.TC_FIELD_V, v)

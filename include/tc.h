@@ -102,7 +102,8 @@ typedef struct {
     double energy;          /* (1/2) <|u|^2> over the volume */
 } tc_stats;
 
-/* Create a case with the default box of Sec. 4 and float64 precision.
+/* Create a case with the default box of Sec. 4, float64 precision and the
+ * tile autotuner on.
  * Nr >= 9; Ntheta a multiple of 4 and Nz even >= 4, both of the form 2^a 3^b;
  * 0 < zeta < 1; Re > 0;
  * dt > 0.  The state starts as circular Couette flow (Eq. 1, W(R_o) =

@@ -326,6 +326,9 @@ int init_handle(tc_handle* h) {
     d.prec = P.precision;
     d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
     d.line_block = 128;
+    d.fscale = 1.0 / ((double)d.Mt * (double)d.Mz);
+    d.fscale_f = (float)d.fscale;
+    d.fscale_lo = (float)(d.fscale - (double)d.fscale_f);
     d.dt = P.dt;
     d.nu = 2.0 / P.Re_inner;
     d.W_outer = P.Re_outer / P.Re_inner;
@@ -583,7 +586,7 @@ tc_handle* tc_create(int Nr, int Ntheta, int Nz, double radius_ratio, double Re_
     std::memset(&p, 0, sizeof(p));
     p.Nr = Nr; p.Ntheta = Ntheta; p.Nz = Nz; p.radius_ratio = radius_ratio;
     p.Re_inner = Re_inner; p.Re_outer = Re_outer; p.dt = dt;
-    p.Theta = 0.0; p.Lz = 0.0; p.precision = TC_PREC_FP64; p.device = -1;
+    p.Theta = 0.0; p.Lz = 0.0; p.precision = TC_PREC_FP64; p.device = -1; p.autotune = 1;
     return tc_create_ex(&p);
 }
 

@@ -396,7 +396,10 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
     }
     __syncthreads();
     C* res = fft<T, -1>(buf0, buf1, ct, d.pz, twz<T>(d));
-    const T scale = (T)(1.0 / ((double)d.Mt * (double)d.Mz));
+    T scale;
+    if constexpr (std::is_same<T, double>::value) scale = d.fscale;
+    else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;
+    else scale = dfloat(d.fscale_f, d.fscale_lo);
     // products: double2 for float64, float2 for the mixed form, double-float
     // pairs for the double-float form (read as such by the line kernel)
     typedef typename std::conditional<std::is_same<T, double>::value, double2, C>::type PO;

@@ -29,6 +29,9 @@ struct TcDev {
     int ztile;                  // azimuthal columns per CTA of the z kernels (divides Nh)
     int line_block;             // threads per block of the line kernel
     double dt, nu, m0, alpha0, W_outer;
+    double fscale;              // 1/(Mt Mz), the forward-transform factor
+    float fscale_f;
+    float fscale_lo;            // fscale - (double)fscale_f: double-float low part
     // RK coefficients of substep k and of the substep after it
     double rk_alpha[3], rk_beta[3], rk_gamma[3], rk_zeta[3];
 
