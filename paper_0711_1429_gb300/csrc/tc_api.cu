@@ -172,15 +172,22 @@ bool build_stencils(const std::vector<double>& r, HostStencils& S) {
     return true;
 }
 
-// Mixed-radix Stockham plan: radix-3 stages first, then 4, then 2.
-bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim) {
+// Mixed-radix Stockham plans.  Family 0 (theta rows): radix-3 stages first,
+// then 4, then 2.  Family 1 (z columns): radix-3 stages, then 16, then one
+// stage of 8, 4 or 2.
+bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim, int family) {
     p.M = M;
     p.nst = 0;
     int m = M, Ns = 1, off = 0;
     std::vector<int> radices;
     while (m % 3 == 0) { radices.push_back(3); m /= 3; }
-    while (m % 4 == 0) { radices.push_back(4); m /= 4; }
-    while (m % 2 == 0) { radices.push_back(2); m /= 2; }
+    if (family == 0) {
+        while (m % 4 == 0) { radices.push_back(4); m /= 4; }
+        while (m % 2 == 0) { radices.push_back(2); m /= 2; }
+    } else {
+        while (m % 16 == 0) { radices.push_back(16); m /= 16; }
+        if (m == 2 || m == 4 || m == 8) { radices.push_back(m); m = 1; }
+    }
     if (m != 1 || (int)radices.size() > TC_MAX_STAGES) return false;
     const ld twopi = 6.283185307179586476925286766559005768L;
     for (int R : radices) {
@@ -216,8 +223,8 @@ void set_err(const std::string& s) { g_err = s; }
 using tcx::set_err;
 
 // Used by the allocation-free transform entry point (tc_noalloc.cu).
-bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im) {
-    return make_plan(M, p, re, im);
+bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im, int family) {
+    return make_plan(M, p, re, im, family);
 }
 void tc_set_error_message(const std::string& s) { set_err(s); }
 
@@ -297,7 +304,7 @@ int autotune(tc_handle* h) {
     d.ztile = best_t;
     best = 1e30f;
     int best_b = d.line_block;
-    for (int bs : {64, 128, 256}) {
+    for (int bs : {64, 128, 256, 1003, 1004}) {
         d.line_block = bs;
         const float ms = timed([&] { tc_launch_line_phase(d, 0, h->stream); });
         if (ms < best) { best = ms; best_b = bs; }
@@ -385,7 +392,7 @@ int init_handle(tc_handle* h) {
     }
     // FFT plans
     std::vector<ld> zr, zi, tr, ti, hr, hi;
-    if (!make_plan(d.Mz, d.pz, zr, zi) || !make_plan(d.Mt, d.pt, tr, ti) || !make_plan(d.Mt / 2, d.ph, hr, hi)) {
+    if (!make_plan(d.Mz, d.pz, zr, zi, 1) || !make_plan(d.Mt, d.pt, tr, ti, 0) || !make_plan(d.Mt / 2, d.ph, hr, hi, 0)) {
         set_err("FFT length is not of the form 2^a 3^b");
         return TC_ERR_ARG;
     }

@@ -17,7 +17,8 @@
 //             gradient, which the pressure-free v and eta rows annihilate.
 //   k_zfwd  : per (product, r, tile): forward complex FFT in z, truncation to
 //             the Nz slots and scaling by 1/(Mt Mz).
-// All transforms are mixed-radix (4, 3, 2) Stockham FFTs in shared memory.
+// All transforms are mixed-radix (3, 16, then 8, 4 or 2) Stockham FFTs in
+// shared memory.
 // Template parameter T is the arithmetic type (double, or float in the
 // mixed-precision form).
 #include "tc_internal.h"
@@ -59,11 +60,94 @@ template <int SIGN, typename C> __device__ __forceinline__ C c_si(C a) {
     return r;
 }
 
+// ---- butterflies ------------------------------------------------------------
+// x * (re + i im) for a constant
+template <typename C, typename T> __device__ __forceinline__ C c_mulc(C a, T re, T im) {
+    C r;
+    r.x = a.x * re - a.y * im;
+    r.y = a.x * im + a.y * re;
+    return r;
+}
+template <int SIGN, typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+    C a0 = c_add(v0, v2), a1 = c_sub(v0, v2), a2 = c_add(v1, v3), a3 = c_si<SIGN>(c_sub(v1, v3));
+    v0 = c_add(a0, a2); v1 = c_add(a1, a3); v2 = c_sub(a0, a2); v3 = c_sub(a1, a3);
+}
+// In-place R-point DFT X_k = sum_r v_r exp(SIGN 2 pi i r k/R); output k lands
+// in v[dft_slot<R>(k)].
+template <int R> __host__ __device__ constexpr int dft_slot(int k) { return R == 16 ? 4 * (k % 4) + k / 4 : k; }
+template <int R, int SIGN, typename T, typename C> __device__ __forceinline__ void dft(C* v) {
+    if constexpr (R == 2) {
+        C a = c_add(v[0], v[1]), b = c_sub(v[0], v[1]);
+        v[0] = a; v[1] = b;
+    } else if constexpr (R == 3) {
+        const T h = (T)0.5;
+        const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
+        C sm = c_add(v[1], v[2]), df = c_sub(v[1], v[2]);
+        C t0; t0.x = v[0].x - h * sm.x; t0.y = v[0].y - h * sm.y;
+        C id = c_si<SIGN>(df); id.x *= s3; id.y *= s3;
+        v[0] = c_add(v[0], sm);
+        v[1] = c_add(t0, id);
+        v[2] = c_sub(t0, id);
+    } else if constexpr (R == 4) {
+        dft4<SIGN>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        // even and odd halves, then X_k = E_k + w^k O_k, X_{k+4} = E_k - w^k O_k
+        dft4<SIGN>(v[0], v[2], v[4], v[6]);
+        dft4<SIGN>(v[1], v[3], v[5], v[7]);
+        const T c = (T)0.70710678118654752440;   // cos(pi/4)
+        const T sc = SIGN > 0 ? c : -c;
+        C o1 = c_mulc(v[3], c, sc);              // w = exp(SIGN i pi/4)
+        C o2 = c_si<SIGN>(v[5]);                 // w^2 = SIGN i
+        C o3 = c_mulc(v[7], -c, sc);             // w^3
+        C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+        v[0] = c_add(e0, o0); v[4] = c_sub(e0, o0);
+        v[1] = c_add(e1, o1); v[5] = c_sub(e1, o1);
+        v[2] = c_add(e2, o2); v[6] = c_sub(e2, o2);
+        v[3] = c_add(e3, o3); v[7] = c_sub(e3, o3);
+    } else {   // R == 16: 4 x 4 with internal twiddles exp(SIGN 2 pi i j k/16)
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) dft4<SIGN>(v[j], v[j + 4], v[j + 8], v[j + 12]);
+        const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;   // pi/8
+        const T c2 = (T)0.70710678118654752440;
+        const T sg = SIGN > 0 ? (T)1 : (T)-1;
+        // element j + 4 k1 holds Y_j[k1]; multiply by w16^(j k1)
+        v[5] = c_mulc(v[5], c1, sg * s1);            // j=1,k1=1: e=1
+        v[9] = c_mulc(v[9], c2, sg * c2);            // j=1,k1=2: e=2
+        v[13] = c_mulc(v[13], s1, sg * c1);          // j=1,k1=3: e=3
+        v[6] = c_mulc(v[6], c2, sg * c2);            // j=2,k1=1: e=2
+        v[10] = c_si<SIGN>(v[10]);                   // j=2,k1=2: e=4
+        v[14] = c_mulc(v[14], -c2, sg * c2);         // j=2,k1=3: e=6
+        v[7] = c_mulc(v[7], s1, sg * c1);            // j=3,k1=1: e=3
+        v[11] = c_mulc(v[11], -c2, sg * c2);         // j=3,k1=2: e=6
+        v[15] = c_mulc(v[15], -c1, -sg * s1);        // j=3,k1=3: e=9
+        #pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    }
+}
+
+// One Stockham butterfly: reads src[j + r M/R], twiddles by
+// exp(SIGN 2 pi i r (j mod Ns)/(Ns R)), R-point DFT, writes
+// dst[(j/Ns) Ns R + (j mod Ns) + r Ns].
+template <int R, int SIGN, typename T, typename C>
+__device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int nb, int Ns, const C* tws) {
+    C v[R];
+    const int jm = j % Ns;
+    #pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sc[j + r * nb];
+    if (Ns > 1) {
+        const C* t = tws + jm * (R - 1);
+        #pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = c_tw<SIGN>(v[r], t[r - 1]);
+    }
+    dft<R, SIGN, T>(v);
+    C* dc = dcol + (j / Ns) * Ns * R + jm;
+    #pragma unroll
+    for (int r = 0; r < R; ++r) dc[r * Ns] = v[dft_slot<R>(r)];
+}
+
 // ncols transforms of length pl.M stored contiguously in buf0 (column c at
-// c*M).  Returns the buffer that holds the result (buf0 or buf1).
-// Each stage: butterfly j of a column reads src[j + r*M/R], applies the
-// twiddles exp(SIGN 2 pi i r (j mod Ns)/(Ns R)), an R-point DFT, and writes
-// dst[(j/Ns) Ns R + (j mod Ns) + r Ns]  (Stockham auto-sort).
+// c*M), with the plan chosen at run time.  Returns the buffer holding the
+// result (buf0 or buf1).
 template <typename T, int SIGN>
 __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<T>::t* buf1,
                                            int ncols, const FftPlan& pl,
@@ -79,39 +163,14 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
         for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
             const int col = b / nb;
             const int j = b - col * nb;
-            const int jm = j % Ns;
             const C* sc = src + col * M;
-            C* dc = dst + col * M + (j / Ns) * Ns * R + jm;
-            if (R == 4) {
-                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb], v3 = sc[j + 3 * nb];
-                if (Ns > 1) {
-                    const C* t = tws + jm * 3;
-                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]); v3 = c_tw<SIGN>(v3, t[2]);
-                }
-                C a0 = c_add(v0, v2), a1 = c_sub(v0, v2), a2 = c_add(v1, v3), a3 = c_si<SIGN>(c_sub(v1, v3));
-                dc[0] = c_add(a0, a2);
-                dc[Ns] = c_add(a1, a3);
-                dc[2 * Ns] = c_sub(a0, a2);
-                dc[3 * Ns] = c_sub(a1, a3);
-            } else if (R == 3) {
-                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb];
-                if (Ns > 1) {
-                    const C* t = tws + jm * 2;
-                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]);
-                }
-                const T h = (T)0.5;
-                const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
-                C sm = c_add(v1, v2), df = c_sub(v1, v2);
-                C t0; t0.x = v0.x - h * sm.x; t0.y = v0.y - h * sm.y;
-                C id = c_si<SIGN>(df); id.x *= s3; id.y *= s3;
-                dc[0] = c_add(v0, sm);
-                dc[Ns] = c_add(t0, id);
-                dc[2 * Ns] = c_sub(t0, id);
-            } else {  // R == 2
-                C v0 = sc[j], v1 = sc[j + nb];
-                if (Ns > 1) v1 = c_tw<SIGN>(v1, tws[jm]);
-                dc[0] = c_add(v0, v1);
-                dc[Ns] = c_sub(v0, v1);
+            C* dcol = dst + col * M;
+            switch (R) {
+                case 2: stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+                case 3: stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+                case 4: stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+                case 8: stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+                default: stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
             }
         }
         __syncthreads();
@@ -121,94 +180,66 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
 }
 
 // ---- compile-time plans ------------------------------------------------------
-// The same mixed-radix plan (radix-3 stages, then 4, then 2; twiddle offsets
+// The same mixed-radix plans as on the host (families below; twiddle offsets
 // as on the host) with the length known at compile time: every division by
 // the stage constants becomes a multiply-shift and the stage loop unrolls.
-__host__ __device__ constexpr int plan_nst(int M) {
-    int n = 0;
-    while (M % 3 == 0) { M /= 3; ++n; }
-    while (M % 4 == 0) { M /= 4; ++n; }
-    while (M % 2 == 0) { M /= 2; ++n; }
-    return n;
-}
-__host__ __device__ constexpr int plan_radix(int M, int s) {
+// Family 0 (theta rows, few columns per block: many small butterflies):
+// radix-3 stages, then 4, then 2.  Family 1 (z columns, many columns per
+// block): radix-3 stages, then 16, then one stage of 8, 4 or 2.
+__host__ __device__ constexpr int plan_radix_f(int M, int s, int F) {
     int i = 0;
     while (M % 3 == 0) { if (i == s) return 3; M /= 3; ++i; }
-    while (M % 4 == 0) { if (i == s) return 4; M /= 4; ++i; }
-    while (M % 2 == 0) { if (i == s) return 2; M /= 2; ++i; }
-    return 1;
+    if (F == 0) {
+        while (M % 4 == 0) { if (i == s) return 4; M /= 4; ++i; }
+        while (M % 2 == 0) { if (i == s) return 2; M /= 2; ++i; }
+        return 1;
+    }
+    while (M % 16 == 0) { if (i == s) return 16; M /= 16; ++i; }
+    return (i == s) ? M : 1;     // the one remainder stage (8, 4, 2), or none
 }
-__host__ __device__ constexpr int plan_ns(int M, int s) {
+__host__ __device__ constexpr int plan_nst_f(int M, int F) {
+    int n = 0;
+    while (plan_radix_f(M, n, F) > 1) ++n;
+    return n;
+}
+__host__ __device__ constexpr int plan_ns_f(int M, int s, int F) {
     int ns = 1;
-    for (int i = 0; i < s; ++i) ns *= plan_radix(M, i);
+    for (int i = 0; i < s; ++i) ns *= plan_radix_f(M, i, F);
     return ns;
 }
-__host__ __device__ constexpr int plan_off(int M, int s) {
+__host__ __device__ constexpr int plan_off_f(int M, int s, int F) {
     int o = 0;
-    for (int i = 0; i < s; ++i) o += plan_ns(M, i) * (plan_radix(M, i) - 1);
+    for (int i = 0; i < s; ++i) o += plan_ns_f(M, i, F) * (plan_radix_f(M, i, F) - 1);
     return o;
 }
 
-template <typename T, int SIGN, int M, int S>
+template <typename T, int SIGN, int M, int F, int S>
 __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t* src, typename V2<T>::t* dst,
                                                               int ncols, const typename V2<T>::t* __restrict__ tw) {
     typedef typename V2<T>::t C;
-    if constexpr (S == plan_nst(M)) {
+    if constexpr (S == plan_nst_f(M, F)) {
         return src;
     } else {
-        constexpr int R = plan_radix(M, S);
-        constexpr int Ns = plan_ns(M, S);
+        constexpr int R = plan_radix_f(M, S, F);
+        constexpr int Ns = plan_ns_f(M, S, F);
         constexpr int nb = M / R;
-        const C* tws = tw + plan_off(M, S);
+        const C* tws = tw + plan_off_f(M, S, F);
         for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
             const int col = b / nb;
             const int j = b - col * nb;
-            const int jm = j % Ns;
-            const C* sc = src + col * M;
-            C* dc = dst + col * M + (j / Ns) * Ns * R + jm;
-            if constexpr (R == 4) {
-                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb], v3 = sc[j + 3 * nb];
-                if constexpr (Ns > 1) {
-                    const C* t = tws + jm * 3;
-                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]); v3 = c_tw<SIGN>(v3, t[2]);
-                }
-                C a0 = c_add(v0, v2), a1 = c_sub(v0, v2), a2 = c_add(v1, v3), a3 = c_si<SIGN>(c_sub(v1, v3));
-                dc[0] = c_add(a0, a2);
-                dc[Ns] = c_add(a1, a3);
-                dc[2 * Ns] = c_sub(a0, a2);
-                dc[3 * Ns] = c_sub(a1, a3);
-            } else if constexpr (R == 3) {
-                C v0 = sc[j], v1 = sc[j + nb], v2 = sc[j + 2 * nb];
-                if constexpr (Ns > 1) {
-                    const C* t = tws + jm * 2;
-                    v1 = c_tw<SIGN>(v1, t[0]); v2 = c_tw<SIGN>(v2, t[1]);
-                }
-                const T h = (T)0.5;
-                const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
-                C sm = c_add(v1, v2), df = c_sub(v1, v2);
-                C t0; t0.x = v0.x - h * sm.x; t0.y = v0.y - h * sm.y;
-                C id = c_si<SIGN>(df); id.x *= s3; id.y *= s3;
-                dc[0] = c_add(v0, sm);
-                dc[Ns] = c_add(t0, id);
-                dc[2 * Ns] = c_sub(t0, id);
-            } else {
-                C v0 = sc[j], v1 = sc[j + nb];
-                if constexpr (Ns > 1) v1 = c_tw<SIGN>(v1, tws[jm]);
-                dc[0] = c_add(v0, v1);
-                dc[Ns] = c_sub(v0, v1);
-            }
+            stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
         }
         __syncthreads();
-        return fft_fixed_stage<T, SIGN, M, S + 1>(dst, src, ncols, tw);
+        return fft_fixed_stage<T, SIGN, M, F, S + 1>(dst, src, ncols, tw);
     }
 }
 
 // Dispatch on the transform length: compile-time plans for the lengths of
 // the supported grids, the run-time plan otherwise (same arithmetic).
-template <typename T, int SIGN>
+template <typename T, int SIGN, int F>
 __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw) {
-#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, 0>(buf0, buf1, ncols, tw);
+#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0>(buf0, buf1, ncols, tw);
     switch (pl.M) {
         TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
         TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
@@ -264,7 +295,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, +1, 1>(buf0, buf1, ct, d.pz, twz<T>(d));
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
@@ -328,8 +359,8 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         hA[k] = z;
     }
     __syncthreads();
-    C* r1 = fft<T, +1>(fA, fB, 1, d.pt, twt<T>(d));
-    C* r2 = fft<T, +1>(hA, hB, 1, d.ph, twh<T>(d));
+    C* r1 = fft<T, +1, 0>(fA, fB, 1, d.pt, twt<T>(d));
+    C* r2 = fft<T, +1, 0>(hA, hB, 1, d.ph, twh<T>(d));
     C* o1 = (r1 == fA) ? fB : fA;
     C* o2 = (r2 == hA) ? hB : hA;
     for (int m = threadIdx.x; m < H; m += blockDim.x) {
@@ -349,8 +380,8 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         o2[m] = z;
     }
     __syncthreads();
-    C* out = fft<T, -1>(o1, r1, 2, d.pt, twt<T>(d));
-    C* out2 = fft<T, -1>(o2, r2, 1, d.ph, twh<T>(d));
+    C* out = fft<T, -1, 0>(o1, r1, 2, d.pt, twt<T>(d));
+    C* out2 = fft<T, -1, 0>(o2, r2, 1, d.ph, twh<T>(d));
     C* pb = reinterpret_cast<C*>(d.pbuf);
     for (int idx = threadIdx.x; idx < 3 * Nh; idx += blockDim.x) {
         const int c = idx / Nh, j = idx - c * Nh;
@@ -395,7 +426,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
-    C* res = fft<T, -1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, -1, 1>(buf0, buf1, ct, d.pz, twz<T>(d));
     T scale;
     if constexpr (std::is_same<T, double>::value) scale = d.fscale;
     else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;

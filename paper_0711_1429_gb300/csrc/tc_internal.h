@@ -27,7 +27,8 @@ struct TcDev {
     int mixed;                  // 1: float32 FFT/products (precision == TC_PREC_MIXED)
     int prec;                   // TC_PREC_FP64, TC_PREC_MIXED or TC_PREC_DF64
     int ztile;                  // azimuthal columns per CTA of the z kernels (divides Nh)
-    int line_block;             // threads per block of the line kernel
+    int line_block;             // line-kernel variant: 64/128/256 threads, or 1003/1004 =
+                                // 128 threads with registers for 3/4 resident blocks per SM
     double dt, nu, m0, alpha0, W_outer;
     double fscale;              // 1/(Mt Mz), the forward-transform factor
     float fscale_f;

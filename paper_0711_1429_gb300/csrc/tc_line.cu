@@ -356,8 +356,8 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 // explicit rows are formed in double-float arithmetic (float32 pipe) from the
 // double-float products; the right sides, the solves, the RK memory and the
 // reconstruction are float64 in every form.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_line(TcDev d, int k) {
+template <int MODE, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
     constexpr bool MIXED = (MODE == 1);
     typedef typename LineTypes<MODE>::T T;
     typedef typename LineTypes<MODE>::CT CT;
@@ -799,10 +799,23 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
 }
 
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
-    const int bs = d.line_block > 0 ? d.line_block : 128;
-    if (d.prec == 1) k_line<1><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
-    else if (d.prec == 2) k_line<2><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
-    else k_line<0><<<(d.npairs + bs - 1) / bs, bs, 0, s>>>(d, k);
+    // line_block encodes the variant: 64/128/256 threads with the register
+    // budget of one 256-thread block per SM, or 128 threads with a budget
+    // for 3 (1003) or 4 (1004) resident blocks per SM
+    const int v = d.line_block > 0 ? d.line_block : 128;
+    const int bs = v > 1000 ? 128 : v;
+    const int grid = (d.npairs + bs - 1) / bs;
+    switch (d.prec * 10 + (v == 1003 ? 1 : v == 1004 ? 2 : 0)) {
+        case 0:  k_line<0, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
+        case 1:  k_line<0, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
+        case 2:  k_line<0, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+        case 10: k_line<1, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
+        case 11: k_line<1, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
+        case 12: k_line<1, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+        case 20: k_line<2, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
+        case 21: k_line<2, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
+        default: k_line<2, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+    }
 }
 
 static size_t mean_smem(const TcDev& d) { return (size_t)(2 * d.Nr * 5 * 2 + 2 * d.Nr * 3) * sizeof(double); }

@@ -23,7 +23,7 @@
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TC_NOALLOC_SCRATCH_BYTES];
 
-bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im);
+bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im, int family);
 void tc_set_error_message(const std::string& s);
 
 namespace {
@@ -92,7 +92,7 @@ extern "C" int tc_to_physical_noalloc(int Nr, int Ntheta, int Nz, const void* sp
     d.npairs = d.Nz * d.Nh;
     d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
     std::vector<long double> zr, zi, tr, ti;
-    if (!tc_build_fft_plan(d.Mz, d.pz, zr, zi) || !tc_build_fft_plan(d.Mt, d.pt, tr, ti)) {
+    if (!tc_build_fft_plan(d.Mz, d.pz, zr, zi, 1) || !tc_build_fft_plan(d.Mt, d.pt, tr, ti, 0)) {
         tc_set_error_message("tc_to_physical_noalloc: FFT length is not of the form 2^a 3^b");
         return TC_ERR_ARG;
     }
