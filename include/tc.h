@@ -89,6 +89,10 @@ typedef struct {
                                transforms and the line-phase block size at
                                creation and keep the fastest (cached per shape
                                class); results do not depend on the choice     */
+    double stretch;         /* radial grid: 0 uniform; a > 0 the tanh map
+                               r_j = (R_i + 1) + tanh(a s_j)/tanh(a),
+                               s_j = -1 + 2j/(Nr-1), denser at both walls (the
+                               paper's grid is "smoothly stretched", Sec. 2.1) */
 } tc_params;
 
 typedef struct {

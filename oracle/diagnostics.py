@@ -39,16 +39,18 @@ def re_tau(case, S, W):
     return math.sqrt(nu * si) / nu, math.sqrt(nu * so) / nu
 
 
-def radial_weights(r):
-    """Fourth-order quadrature on a uniform grid (trapezoid with end
-    corrections 3/8, 7/6, 23/24)."""
+def radial_weights(r, stretch=0.0):
+    """Fourth-order quadrature in the grid coordinate s (uniform), trapezoid
+    with end corrections 3/8, 7/6, 23/24, times the Jacobian dr/ds of the
+    radial map (1 on the uniform grid)."""
+    from .grid import radial_jacobian
     N = len(r)
-    h = (r[-1] - r[0]) / (N - 1)
+    h = 2.0 / (N - 1) if stretch != 0.0 else (r[-1] - r[0]) / (N - 1)
     w = np.ones(N)
     w[[0, -1]] = 3.0 / 8.0
     w[[1, -2]] = 7.0 / 6.0
     w[[2, -3]] = 23.0 / 24.0
-    return h * w
+    return h * w * radial_jacobian(N, stretch)
 
 
 def kinetic_energy(case, u, v, w):
@@ -57,5 +59,5 @@ def kinetic_energy(case, u, v, w):
     wt[0] = 1.0
     spec = (np.abs(u) ** 2 + np.abs(v) ** 2 + np.abs(w) ** 2) * wt[None, None, :]
     prof = spec.sum(axis=(1, 2))
-    q = radial_weights(case.r) * case.r
+    q = radial_weights(case.r, case.stretch) * case.r
     return 0.5 * float(np.dot(q, prof) / np.sum(q))

@@ -21,16 +21,30 @@ import math
 import numpy as np
 
 
-def radial_grid(zeta, Nr):
-    """Uniform radial grid from R_i to R_i + 2 (units of h).
+def radial_grid(zeta, Nr, stretch=0.0):
+    """Radial grid from R_i to R_i + 2 (units of h).
 
     R_i = 2 zeta / (1 - zeta) follows from zeta = R_i/R_o and R_o - R_i = 2.
-    The points are formed as R_i + (2 j)/(Nr - 1) in float64, in exactly that
-    order of operations.
+    Uniform (stretch = 0): r_j = R_i + (2 j)/(Nr - 1).  The paper uses a
+    smoothly stretched grid (Sec. 2.1; Table 4 gives a finer spacing at the
+    walls than at the centre) without giving the map; the reading used here
+    is the tanh map r_j = (R_i + 1) + tanh(a s_j)/tanh(a) with
+    s_j = -1 + (2 j)/(Nr - 1), a = stretch > 0 (denser at both walls).
     """
     Ri = 2.0 * zeta / (1.0 - zeta)
     j = np.arange(Nr, dtype=np.float64)
-    return Ri + (2.0 * j) / float(Nr - 1)
+    if stretch == 0.0:
+        return Ri + (2.0 * j) / float(Nr - 1)
+    s = -1.0 + (2.0 * j) / float(Nr - 1)
+    return (Ri + 1.0) + np.tanh(stretch * s) / np.tanh(stretch)
+
+
+def radial_jacobian(Nr, stretch=0.0):
+    """dr/ds at the grid points of the map above (1 for the uniform grid)."""
+    if stretch == 0.0:
+        return np.ones(Nr)
+    s = -1.0 + (2.0 * np.arange(Nr)) / float(Nr - 1)
+    return stretch * (1.0 - np.tanh(stretch * s) ** 2) / np.tanh(stretch)
 
 
 @dataclass
@@ -45,6 +59,7 @@ class Case:
     dt: float
     Theta: float = None      # azimuthal extent of the box (radians)
     Lz: float = 5.0          # axial extent of the box (units of h)
+    stretch: float = 0.0     # tanh stretching of the radial grid (0: uniform)
     r: np.ndarray = field(init=False, repr=False)
 
     def __post_init__(self):
@@ -68,7 +83,7 @@ class Case:
         self.alpha0 = 2.0 * math.pi / self.Lz
         self.nu = 2.0 / self.Re_i
         self.W_outer = self.Re_o / self.Re_i
-        self.r = radial_grid(self.zeta, self.Nr)
+        self.r = radial_grid(self.zeta, self.Nr, self.stretch)
         self.Nh = self.Ntheta // 2
         self.Mt = 3 * self.Ntheta // 2
         self.Mz = 3 * self.Nz // 2

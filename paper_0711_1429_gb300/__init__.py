@@ -32,7 +32,8 @@ class tc_params(ctypes.Structure):
                 ("radius_ratio", ctypes.c_double), ("Re_inner", ctypes.c_double),
                 ("Re_outer", ctypes.c_double), ("dt", ctypes.c_double),
                 ("Theta", ctypes.c_double), ("Lz", ctypes.c_double),
-                ("precision", ctypes.c_int), ("device", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("device", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("stretch", ctypes.c_double)]
 
 
 class tc_stats(ctypes.Structure):
@@ -152,13 +153,15 @@ def tc_create(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt):
 
 
 def make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0, Lz=0.0,
-                precision=TC_PREC_FP64, device=-1, autotune=0):
-    return tc_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device, autotune)
+                precision=TC_PREC_FP64, device=-1, autotune=0, stretch=0.0):
+    return tc_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device,
+                     autotune, stretch)
 
 
 def tc_create_ex(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0, Lz=0.0,
-                 precision=TC_PREC_FP64, device=-1, autotune=0):
-    p = make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device, autotune)
+                 precision=TC_PREC_FP64, device=-1, autotune=0, stretch=0.0):
+    p = make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device,
+                    autotune, stretch)
     h = lib().tc_create_ex(ctypes.byref(p))
     if not h:
         raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())

@@ -342,7 +342,19 @@ int init_handle(tc_handle* h) {
     // grid: R_i = 2 zeta/(1 - zeta), r_j = R_i + (2 j)/(Nr - 1)
     const double Ri = 2.0 * P.radius_ratio / (1.0 - P.radius_ratio);
     h->r.resize(P.Nr);
-    for (int j = 0; j < P.Nr; ++j) h->r[j] = Ri + (2.0 * (double)j) / (double)(P.Nr - 1);
+    h->jac.assign(P.Nr, 1.0);
+    if (P.stretch == 0.0) {
+        for (int j = 0; j < P.Nr; ++j) h->r[j] = Ri + (2.0 * (double)j) / (double)(P.Nr - 1);
+    } else {
+        // tanh map, denser at both walls
+        const double ta = std::tanh(P.stretch);
+        for (int j = 0; j < P.Nr; ++j) {
+            const double sj = -1.0 + (2.0 * (double)j) / (double)(P.Nr - 1);
+            const double t = std::tanh(P.stretch * sj);
+            h->r[j] = (Ri + 1.0) + t / ta;
+            h->jac[j] = P.stretch * (1.0 - t * t) / ta;
+        }
+    }
     h->Ri = Ri;
     h->Ro = h->r[P.Nr - 1];
     const double rc = Ri + 1.0;
@@ -538,6 +550,7 @@ int validate(const tc_params* p) {
     if (!(p->radius_ratio > 0.0 && p->radius_ratio < 1.0)) { set_err("radius ratio must lie in (0, 1)"); return TC_ERR_ARG; }
     if (!(p->Re_inner > 0.0) || !std::isfinite(p->Re_outer)) { set_err("Re_inner must be > 0 and Re_outer finite"); return TC_ERR_ARG; }
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { set_err("dt must be > 0"); return TC_ERR_ARG; }
+    if (!(p->stretch >= 0.0 && p->stretch <= 8.0)) { set_err("stretch must lie in [0, 8]"); return TC_ERR_ARG; }
     if (p->precision != TC_PREC_FP64 && p->precision != TC_PREC_MIXED && p->precision != TC_PREC_DF64) { set_err("unknown precision"); return TC_ERR_ARG; }
     return TC_OK;
 }
@@ -593,7 +606,7 @@ tc_handle* tc_create(int Nr, int Ntheta, int Nz, double radius_ratio, double Re_
     std::memset(&p, 0, sizeof(p));
     p.Nr = Nr; p.Ntheta = Ntheta; p.Nz = Nz; p.radius_ratio = radius_ratio;
     p.Re_inner = Re_inner; p.Re_outer = Re_outer; p.dt = dt;
-    p.Theta = 0.0; p.Lz = 0.0; p.precision = TC_PREC_FP64; p.device = -1; p.autotune = 1;
+    p.Theta = 0.0; p.Lz = 0.0; p.precision = TC_PREC_FP64; p.device = -1; p.autotune = 1; p.stretch = 0.0;
     return tc_create_ex(&p);
 }
 
@@ -761,13 +774,13 @@ int tc_torque_stats(tc_handle* h, tc_stats* out) {
     // fourth-order radial quadrature with weight r (uniform grid):
     // trapezoid with end weights 3/8, 7/6, 23/24
     double num = 0, den = 0;
-    const double hh = (h->r[N - 1] - h->r[0]) / (N - 1);
+    const double hh = h->prm.stretch != 0.0 ? 2.0 / (N - 1) : (h->r[N - 1] - h->r[0]) / (N - 1);
     for (int j = 0; j < N; ++j) {
         double w = 1.0;
         if (j == 0 || j == N - 1) w = 3.0 / 8.0;
         else if (j == 1 || j == N - 2) w = 7.0 / 6.0;
         else if (j == 2 || j == N - 3) w = 23.0 / 24.0;
-        w *= hh * h->r[j];
+        w *= hh * h->jac[j] * h->r[j];
         num += w * ep[j];
         den += w;
     }

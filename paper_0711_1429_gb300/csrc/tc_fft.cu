@@ -148,7 +148,7 @@ __device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int n
 // ncols transforms of length pl.M stored contiguously in buf0 (column c at
 // c*M), with the plan chosen at run time.  Returns the buffer holding the
 // result (buf0 or buf1).
-template <typename T, int SIGN>
+template <typename T, int SIGN, int F = 1>
 __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<T>::t* buf1,
                                            int ncols, const FftPlan& pl,
                                            const typename V2<T>::t* __restrict__ tw) {
@@ -165,12 +165,14 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
             const int j = b - col * nb;
             const C* sc = src + col * M;
             C* dcol = dst + col * M;
-            switch (R) {
-                case 2: stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-                case 3: stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-                case 4: stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-                case 8: stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-                default: stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+            // family 0 plans use radices 2, 3, 4 only: instantiating only
+            // those keeps the register demand of the theta kernels low
+            if (R == 3) stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            else if (R == 4) stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            else if (R == 2) stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            else if constexpr (F == 1) {
+                if (R == 8) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+                else stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws);
             }
         }
         __syncthreads();
@@ -244,7 +246,7 @@ __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* bu
         TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
         TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
         TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
-        default: return fft_stockham<T, SIGN>(buf0, buf1, ncols, pl, tw);
+        default: return fft_stockham<T, SIGN, F>(buf0, buf1, ncols, pl, tw);
     }
 #undef TC_FFT_CASE
 }
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(256) k_rows_phys(TcDev d) {
         bufA[p] = a;
     }
     __syncthreads();
-    double2* res = fft_stockham<double, +1>(bufA, bufB, 1, d.pt, d.twt_d);
+    double2* res = fft_stockham<double, +1, 0>(bufA, bufB, 1, d.pt, d.twt_d);
     for (int p = threadIdx.x; p < Mt; p += blockDim.x)
         d.phys[((size_t)r * Mz + q) * Mt + p] = res[p].x;
 }

@@ -24,6 +24,7 @@ struct tc_handle {
     double t = 0.0;
     long long step = 0;
     std::vector<double> r;
+    std::vector<double> jac;         // dr/ds of the radial map
     HostStencils S;
     double Ri = 0, Ro = 0;
     cudaStream_t own_stream = nullptr;   // created by the batch / server

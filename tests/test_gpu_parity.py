@@ -298,3 +298,29 @@ def test_df64_form_one_step_129():
         _check(c, s, h, 1e-10)
     finally:
         tc.tc_destroy(h)
+
+
+def test_stretched_grid_parity_and_stats():
+    """tanh-stretched radial grid (denser at the walls): one and ten steps,
+    and the torque/energy statistics, against the oracle."""
+    cfg = dict(Nr=41, Ntheta=32, Nz=24, zeta=0.8, Re_i=600.0, Re_o=0.0, dt=1e-3)
+    v, e = inputs(41, 32, 24, 0.8, 17, "k2", 0.05)
+    c = Case(41, 32, 24, 0.8, 600.0, 0.0, 1e-3, stretch=1.4)
+    s = OracleSolver(c)
+    s.set_fields(v=v, eta=e)
+    h = gpu_case(41, 32, 24, 0.8, 600.0, 0.0, 1e-3, v=v, eta=e, stretch=1.4)
+    try:
+        tc.tc_step(h, 1)
+        s.step(1)
+        _check(c, s, h, 1e-10)
+        tc.tc_step(h, 9)
+        s.step(9)
+        _check(c, s, h, 1e-9)
+        st = tc.tc_torque_stats(h)
+        u, vv, w = s.velocity()
+        Gi, Go = dg.torque(c, s.S, s.W)
+        assert abs(st["G_inner"] - Gi) < 1e-10 * Gi and abs(st["G_outer"] - Go) < 1e-10 * Go
+        E = dg.kinetic_energy(c, u, vv, w)
+        assert abs(st["energy"] - E) < 1e-10 * E
+    finally:
+        tc.tc_destroy(h)
