@@ -387,6 +387,24 @@ def run_gpu(args):
         except Exception as ex:        # reported, not fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[-300:]}
 
+    # ---- the paper's own timed workload (Sec. 3.1: 182 s per step on one
+    # 2.66 GHz Xeon, i.e. 129 x 512 x 170 / 182 = 6.17e4 grid-point steps/s)
+    paper = None
+    if not args.no_forms and args.workload == "tc-257x512x512":
+        wp = WORKLOADS["paper-129x512x170"]
+        vp, ep = initial_perturbation(wp["Nr"], wp["Ntheta"], wp["Nz"], wp["seed"], wp["spectrum"], wp["amp"],
+                                      m0=box_defaults(wp["zeta"])[0], alpha0=box_defaults(wp["zeta"])[1],
+                                      rc=box_defaults(wp["zeta"])[2])
+        gpp = wp["Nr"] * wp["Ntheta"] * wp["Nz"]
+        paper = {"workload": "paper-129x512x170", "paper_value": 6.17e4,
+                 "paper_hardware": "1 x Intel Xeon 2.66 GHz (182 s per step, Sec. 3.1)", "forms": {}}
+        for name in ("fp64", "df64", "mixed"):
+            hp, res = time_form(tc, torch, wp, PREC[name], vp, ep, args, local, dist)
+            tc.tc_destroy(hp)
+            val = gpp * args.steps * world / (res["total_ms"] / 1e3)
+            paper["forms"][name] = {"value": val, "ms_per_step": res["total_ms"] / args.steps,
+                                    "vs_paper": val / 6.17e4, "dtype": DTYPE[name]}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": main["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -398,7 +416,7 @@ def run_gpu(args):
             "latency_ms": {"p50": p50, "p99": p99},
             "gpu_launches": 15 * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clk"],
-            "alu_peaks_tflops": peaks, "forms": forms}
+            "alu_peaks_tflops": peaks, "forms": forms, "paper_workload": paper}
     if rank == 0:
         print(json.dumps(line))
     dist.close()

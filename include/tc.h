@@ -108,7 +108,8 @@ typedef struct {
 
 /* Create a case with the default box of Sec. 4, float64 precision and the
  * tile autotuner on.
- * Nr >= 9; Ntheta a multiple of 4 and Nz even >= 4, both of the form 2^a 3^b;
+ * Nr >= 9; Ntheta a multiple of 4 of the form 2^a 3^b; Nz even >= 4 with prime
+ * factors in {2, 3, 5, 7, 11, 13, 17} (the paper's 170 included);
  * 0 < zeta < 1; Re > 0;
  * dt > 0.  The state starts as circular Couette flow (Eq. 1, W(R_o) =
  * Re_outer/Re_inner) with zero perturbation.  Returns NULL on error. */

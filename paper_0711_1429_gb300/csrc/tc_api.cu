@@ -186,8 +186,12 @@ bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim, 
         while (m % 2 == 0) { radices.push_back(2); m /= 2; }
     } else {
         while (m % 16 == 0) { radices.push_back(16); m /= 16; }
-        if (m == 2 || m == 4 || m == 8) { radices.push_back(m); m = 1; }
+        if (m % 8 == 0) { radices.push_back(8); m /= 8; }
+        else if (m % 4 == 0) { radices.push_back(4); m /= 4; }
+        else if (m % 2 == 0) { radices.push_back(2); m /= 2; }
     }
+    for (int pr : {5, 7, 11, 13, 17})          // prime stages (direct sums)
+        while (m % pr == 0) { radices.push_back(pr); m /= pr; }
     if (m != 1 || (int)radices.size() > TC_MAX_STAGES) return false;
     const ld twopi = 6.283185307179586476925286766559005768L;
     for (int R : radices) {
@@ -201,6 +205,14 @@ bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim, 
                 twim.push_back(sinl(a));
             }
         off += Ns * (R - 1);
+        if (R != 2 && R != 3 && R != 4 && R != 8 && R != 16) {   // R-th roots of a prime stage
+            for (int e = 0; e < R; ++e) {
+                const ld a = -twopi * (ld)e / (ld)R;
+                twre.push_back(cosl(a));
+                twim.push_back(sinl(a));
+            }
+            off += R;
+        }
         Ns *= R;
         p.nst++;
     }
@@ -212,6 +224,14 @@ bool is_2a3b(int n) {
     if (n < 1) return false;
     while (n % 2 == 0) n /= 2;
     while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+// axial sizes: factors 2, 3, 5, 7, 11, 13, 17 (the paper's Nz = 170 = 2 5 17)
+bool is_smooth(int n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5, 7, 11, 13, 17})
+        while (n % p == 0) n /= p;
     return n == 1;
 }
 
@@ -546,7 +566,7 @@ int validate(const tc_params* p) {
     if (!p) { set_err("null parameters"); return TC_ERR_ARG; }
     if (p->Nr < 9) { set_err("Nr must be >= 9"); return TC_ERR_ARG; }
     if (p->Ntheta < 4 || p->Ntheta % 4 || !is_2a3b(p->Ntheta)) { set_err("Ntheta must be a multiple of 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
-    if (p->Nz < 4 || p->Nz % 2 || !is_2a3b(p->Nz)) { set_err("Nz must be even, >= 4 and of the form 2^a 3^b"); return TC_ERR_ARG; }
+    if (p->Nz < 4 || p->Nz % 2 || !is_smooth(p->Nz)) { set_err("Nz must be even, >= 4, with prime factors in {2, 3, 5, 7, 11, 13, 17}"); return TC_ERR_ARG; }
     if (!(p->radius_ratio > 0.0 && p->radius_ratio < 1.0)) { set_err("radius ratio must lie in (0, 1)"); return TC_ERR_ARG; }
     if (!(p->Re_inner > 0.0) || !std::isfinite(p->Re_outer)) { set_err("Re_inner must be > 0 and Re_outer finite"); return TC_ERR_ARG; }
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { set_err("dt must be > 0"); return TC_ERR_ARG; }

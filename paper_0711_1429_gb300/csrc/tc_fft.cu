@@ -145,6 +145,30 @@ __device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int n
     for (int r = 0; r < R; ++r) dc[r * Ns] = v[dft_slot<R>(r)];
 }
 
+// Prime radix R (5, 7, 11, 13, 17) by the direct sum X_k = sum_r v_r w^(r k)
+// with w = exp(SIGN 2 pi i/R); the R roots follow the stage's twiddles.
+template <int SIGN, typename T, typename C>
+__device__ __noinline__ void stockham_bfly_prime(const C* sc, C* dcol, int j, int nb, int Ns, int R, const C* tws) {
+    C v[17];
+    const int jm = j % Ns;
+    for (int r = 0; r < R; ++r) {
+        v[r] = sc[j + r * nb];
+        if (Ns > 1 && r > 0) v[r] = c_tw<SIGN>(v[r], tws[jm * (R - 1) + r - 1]);
+    }
+    const C* roots = tws + Ns * (R - 1);
+    C* dc = dcol + (j / Ns) * Ns * R + jm;
+    for (int k = 0; k < R; ++k) {
+        C acc = v[0];
+        int e = 0;
+        for (int r = 1; r < R; ++r) {
+            e += k;
+            if (e >= R) e -= R;
+            acc = c_add(acc, c_tw<SIGN>(v[r], roots[e]));
+        }
+        dc[k * Ns] = acc;
+    }
+}
+
 // ncols transforms of length pl.M stored contiguously in buf0 (column c at
 // c*M), with the plan chosen at run time.  Returns the buffer holding the
 // result (buf0 or buf1).
@@ -170,9 +194,12 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
             if (R == 3) stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws);
             else if (R == 4) stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws);
             else if (R == 2) stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-            else if constexpr (F == 1) {
-                if (R == 8) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-                else stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            else if (F == 1 && R == 8) {
+                if constexpr (F == 1) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            } else if (F == 1 && R == 16) {
+                if constexpr (F == 1) stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            } else {
+                stockham_bfly_prime<SIGN, T>(sc, dcol, j, nb, Ns, R, tws);
             }
         }
         __syncthreads();

@@ -39,6 +39,13 @@ bool is_2a3b(int n) {
     return n == 1;
 }
 
+bool is_smooth(int n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5, 7, 11, 13, 17})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Device address of the scratch array for the current device (set-up on the
@@ -74,8 +81,9 @@ int scratch_for_current_device(unsigned char** out) {
 
 extern "C" int tc_to_physical_noalloc(int Nr, int Ntheta, int Nz, const void* spectral_dev,
                                       void* physical_dev, void* cuda_stream) {
-    if (Nr < 1 || Ntheta < 4 || Nz < 4 || Ntheta % 2 || Nz % 2 || !is_2a3b(Ntheta) || !is_2a3b(Nz)) {
-        tc_set_error_message("tc_to_physical_noalloc: Nr >= 1; Ntheta, Nz even, >= 4, of the form 2^a 3^b");
+    if (Nr < 1 || Ntheta < 4 || Nz < 4 || Ntheta % 4 || Nz % 2 || !is_2a3b(Ntheta) || !is_smooth(Nz)) {
+        tc_set_error_message("tc_to_physical_noalloc: Nr >= 1; Ntheta a multiple of 4 of the form 2^a 3^b; "
+                             "Nz even >= 4 with prime factors in {2, 3, 5, 7, 11, 13, 17}");
         return TC_ERR_ARG;
     }
     if (!spectral_dev || !physical_dev) {

@@ -110,6 +110,10 @@ WORKLOADS = {
                            dt=1e-3, seed=2, spectrum="k2", amp=0.05, steps=100),
     "tc-257x512x512": dict(Nr=257, Ntheta=512, Nz=512, zeta=0.883, Re_i=3000.0, Re_o=0.0,
                            dt=1e-3, seed=3, spectrum="k2", amp=0.05, steps=500),
+    # the paper's turbulent run (Sec. 4, Table 4): zeta 0.882, Re 10500,
+    # Nr 129, 512 x 170 modes, dt 0.012, disturbances O(1e-4) on all modes
+    "paper-129x512x170": dict(Nr=129, Ntheta=512, Nz=170, zeta=0.882, Re_i=10500.0, Re_o=0.0,
+                              dt=0.012, seed=4, spectrum="k2", amp=1e-4, steps=100),
 }
 
 

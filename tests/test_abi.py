@@ -27,7 +27,7 @@ def test_exports_every_declared_function(lib):
     ((5, 16, 16, 0.883, 200.0, 0.0, 1e-3), "Nr"),
     ((33, 10, 16, 0.883, 200.0, 0.0, 1e-3), "Ntheta"),
     ((33, 18, 16, 0.883, 200.0, 0.0, 1e-3), "Ntheta"),
-    ((33, 16, 14, 0.883, 200.0, 0.0, 1e-3), "Nz"),
+    ((33, 16, 38, 0.883, 200.0, 0.0, 1e-3), "Nz"),
     ((33, 16, 16, 1.0, 200.0, 0.0, 1e-3), "radius ratio"),
     ((33, 16, 16, 0.5, -1.0, 0.0, 1e-3), "Re_inner"),
     ((33, 16, 16, 0.5, 100.0, 0.0, 0.0), "dt"),

@@ -324,3 +324,19 @@ def test_stretched_grid_parity_and_stats():
         assert abs(st["energy"] - E) < 1e-10 * E
     finally:
         tc.tc_destroy(h)
+
+
+@pytest.mark.parametrize("Nz", [10, 14, 34])
+def test_prime_radix_axial_sizes(Nz):
+    """Axial sizes with prime factors 5, 7, 17 (padded 15, 21, 51): the
+    transforms take direct-sum prime stages.  The paper's production grid
+    has Nz = 170 = 2 5 17."""
+    cfg = dict(Nr=21, Ntheta=16, Nz=Nz, zeta=0.85, Re_i=500.0, Re_o=0.0, dt=1e-3)
+    v, e = inputs(21, 16, Nz, 0.85, 31, "k2", 0.05)
+    c, s, h = _pair(cfg, v, e)
+    try:
+        tc.tc_step(h, 2)
+        s.step(2)
+        _check(c, s, h, 1e-10)
+    finally:
+        tc.tc_destroy(h)
