@@ -412,7 +412,9 @@ def run_gpu(args):
             "config": {"workload": args.workload, "Nr": Nr, "Ntheta": Nt, "Nz": Nz,
                        "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
                        "precision": args.precision, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (state ~24 GB)", "device_bytes": device_bytes},
+                       "l2": (f"inputs larger than L2 (state {device_bytes / 1e9:.1f} GB)"
+                              if device_bytes > 129e6 else "state fits in L2 (not flushed)"),
+                       "device_bytes": device_bytes},
             "latency_ms": {"p50": p50, "p99": p99},
             "gpu_launches": 15 * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clk"],

@@ -17,8 +17,8 @@
 //             gradient, which the pressure-free v and eta rows annihilate.
 //   k_zfwd  : per (product, r, tile): forward complex FFT in z, truncation to
 //             the Nz slots and scaling by 1/(Mt Mz).
-// All transforms are mixed-radix (3, 16, then 8, 4 or 2) Stockham FFTs in
-// shared memory.
+// All transforms are mixed-radix Stockham FFTs in shared memory: radix 3,
+// 16, then 8, 4 or 2, then the odd primes 5..17 of the axial length.
 // Template parameter T is the arithmetic type (double, or float in the
 // mixed-precision form).
 #include "tc_internal.h"
@@ -145,27 +145,65 @@ __device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int n
     for (int r = 0; r < R; ++r) dc[r * Ns] = v[dft_slot<R>(r)];
 }
 
-// Prime radix R (5, 7, 11, 13, 17) by the direct sum X_k = sum_r v_r w^(r k)
-// with w = exp(SIGN 2 pi i/R); the R roots follow the stage's twiddles.
-template <int SIGN, typename T, typename C>
-__device__ __noinline__ void stockham_bfly_prime(const C* sc, C* dcol, int j, int nb, int Ns, int R, const C* tws) {
-    C v[17];
+// Odd prime radix R (5, 7, 11, 13, 17).  With w = exp(SIGN 2 pi i/R) and
+// h = (R-1)/2, the inputs pair up as a_j = v_j + v_(R-j), b_j = v_j - v_(R-j)
+// (j = 1..h), and for k = 1..h
+//   X_k     = v_0 + sum_j a_j cos(2 pi j k/R) + SIGN i sum_j b_j sin(2 pi j k/R),
+//   X_(R-k) = the same with the sine sum subtracted,
+// since v_j w^(jk) + v_(R-j) w^(-jk) = a_j cos + SIGN i b_j sin.  That takes
+// about 4 h^2 real multiply-adds per butterfly instead of 4 (R-1)^2 for the
+// direct sum.  The roots (cos, -sin)(2 pi e/R) follow the stage's twiddles.
+template <typename C, typename T> __device__ __forceinline__ C c_axpy_r(C acc, T s, C a) {
+    acc.x = acc.x + s * a.x;
+    acc.y = acc.y + s * a.y;
+    return acc;
+}
+template <int R, int SIGN, typename T, typename C>
+__device__ __noinline__ void stockham_bfly_odd(const C* sc, C* dcol, int j, int nb, int Ns, const C* tws) {
+    constexpr int H = (R - 1) / 2;
+    C v[R];
     const int jm = j % Ns;
-    for (int r = 0; r < R; ++r) {
-        v[r] = sc[j + r * nb];
-        if (Ns > 1 && r > 0) v[r] = c_tw<SIGN>(v[r], tws[jm * (R - 1) + r - 1]);
+    #pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sc[j + r * nb];
+    if (Ns > 1) {
+        const C* t = tws + jm * (R - 1);
+        #pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = c_tw<SIGN>(v[r], t[r - 1]);
     }
     const C* roots = tws + Ns * (R - 1);
+    C x0 = v[0];
+    #pragma unroll
+    for (int q = 1; q <= H; ++q) {
+        const C a = c_add(v[q], v[R - q]), b = c_sub(v[q], v[R - q]);
+        v[q] = a;
+        v[R - q] = b;
+        x0 = c_add(x0, a);
+    }
     C* dc = dcol + (j / Ns) * Ns * R + jm;
-    for (int k = 0; k < R; ++k) {
-        C acc = v[0];
-        int e = 0;
-        for (int r = 1; r < R; ++r) {
-            e += k;
-            if (e >= R) e -= R;
-            acc = c_add(acc, c_tw<SIGN>(v[r], roots[e]));
+    dc[0] = x0;
+    #pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        C p = v[0], s;
+        #pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            const C w = roots[(q * k) % R];          // (cos, -sin)(2 pi q k/R)
+            p = c_axpy_r(p, w.x, v[q]);
+            if (q == 1) { s.x = -w.y * v[R - q].x; s.y = -w.y * v[R - q].y; }
+            else        s = c_axpy_r(s, -w.y, v[R - q]);
         }
-        dc[k * Ns] = acc;
+        const C is = c_si<SIGN>(s);
+        dc[k * Ns] = c_add(p, is);
+        dc[(R - k) * Ns] = c_sub(p, is);
+    }
+}
+template <int SIGN, typename T, typename C>
+__device__ __forceinline__ void stockham_bfly_prime(const C* sc, C* dcol, int j, int nb, int Ns, int R, const C* tws) {
+    switch (R) {
+        case 5: stockham_bfly_odd<5, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+        case 7: stockham_bfly_odd<7, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+        case 11: stockham_bfly_odd<11, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+        case 13: stockham_bfly_odd<13, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+        default: stockham_bfly_odd<17, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
     }
 }
 
@@ -194,11 +232,13 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
             if (R == 3) stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws);
             else if (R == 4) stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws);
             else if (R == 2) stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-            else if (F == 1 && R == 8) {
-                if constexpr (F == 1) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-            } else if (F == 1 && R == 16) {
-                if constexpr (F == 1) stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-            } else {
+            else if (F >= 1 && R == 8) {
+                if constexpr (F >= 1) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            } else if (F >= 1 && R == 16) {
+                if constexpr (F >= 1) stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            } else if constexpr (F == 2) {
+                // odd prime stages: only in the kernels instantiated for axial
+                // lengths with factors 5..17 (their register demand is higher)
                 stockham_bfly_prime<SIGN, T>(sc, dcol, j, nb, Ns, R, tws);
             }
         }
@@ -269,11 +309,15 @@ template <typename T, int SIGN, int F>
 __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw) {
 #define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0>(buf0, buf1, ncols, tw);
-    switch (pl.M) {
-        TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
-        TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
-        TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
-        default: return fft_stockham<T, SIGN, F>(buf0, buf1, ncols, pl, tw);
+    if constexpr (F == 2) {
+        return fft_stockham<T, SIGN, 2>(buf0, buf1, ncols, pl, tw);
+    } else {
+        switch (pl.M) {
+            TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
+            TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
+            TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
+            default: return fft_stockham<T, SIGN, F>(buf0, buf1, ncols, pl, tw);
+        }
     }
 #undef TC_FFT_CASE
 }
@@ -297,7 +341,8 @@ template <> __device__ __forceinline__ const float2* twr<float>(const TcDev& d) 
 
 
 // ---- k_zinv: spectral (u, v, w) -> zbuf[f][r][q][j] ---------------------------
-template <typename T>
+// ZF = 1: axial lengths 2^a 3^b; ZF = 2: lengths with odd prime factors.
+template <typename T, int ZF>
 __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict__ f0,
                                               const double2* __restrict__ f1,
                                               const double2* __restrict__ f2) {
@@ -324,7 +369,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1, 1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, +1, ZF>(buf0, buf1, ct, d.pz, twz<T>(d));
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
@@ -438,7 +483,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
 }
 
 // ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) -----------------
-template <typename T>
+template <typename T, int ZF>
 __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -455,7 +500,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
-    C* res = fft<T, -1, 1>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, -1, ZF>(buf0, buf1, ct, d.pz, twz<T>(d));
     T scale;
     if constexpr (std::is_same<T, double>::value) scale = d.fscale;
     else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;
@@ -520,15 +565,28 @@ __global__ void __launch_bounds__(256) k_energy(TcDev d) {
 }
 
 // ---- host launchers --------------------------------------------------------------
+static bool z_has_odd_primes(const TcDev& d) {
+    for (int i = 0; i < d.pz.nst; ++i)
+        if (d.pz.R[i] % 2 && d.pz.R[i] != 3) return true;
+    return false;
+}
+
 template <typename T>
 static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
     typedef typename V2<T>::t C;
     const int ct = d.ztile;
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
     const size_t smr = 5 * (size_t)d.Mt * sizeof(C);   // 2 x (2 full + 1 half) columns
-    if (which == 0) k_zinv<T><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
-    else if (which == 1) k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
-    else k_zfwd<T><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
+    const bool odd = z_has_odd_primes(d);
+    if (which == 0) {
+        if (odd) k_zinv<T, 2><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
+        else k_zinv<T, 1><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
+    } else if (which == 1) {
+        k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
+    } else {
+        if (odd) k_zfwd<T, 2><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
+        else k_zfwd<T, 1><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
+    }
 }
 
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s) {
@@ -546,7 +604,8 @@ void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s)
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(double2);
     TcDev dd = d;
     // one field through slot 0 of zbuf (always float64 here)
-    k_zinv<double><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
+    if (z_has_odd_primes(d)) k_zinv<double, 2><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
+    else k_zinv<double, 1><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
     k_rows_phys<<<dim3(d.Mz, d.Nr), 256, 2 * (size_t)d.Mt * sizeof(double2), s>>>(dd);
 }
 
@@ -559,10 +618,11 @@ cudaError_t tc_set_kernel_attributes() {
         cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (r != cudaSuccess) e = r;
     };
-    set((const void*)k_zinv<double>); set((const void*)k_zinv<float>);
-    set((const void*)k_rows<double>); set((const void*)k_rows<float>);
-    set((const void*)k_zfwd<double>); set((const void*)k_zfwd<float>);
-    set((const void*)k_zinv<dfloat>); set((const void*)k_rows<dfloat>); set((const void*)k_zfwd<dfloat>);
+    set((const void*)k_zinv<double, 1>); set((const void*)k_zinv<float, 1>); set((const void*)k_zinv<dfloat, 1>);
+    set((const void*)k_zinv<double, 2>); set((const void*)k_zinv<float, 2>); set((const void*)k_zinv<dfloat, 2>);
+    set((const void*)k_zfwd<double, 1>); set((const void*)k_zfwd<float, 1>); set((const void*)k_zfwd<dfloat, 1>);
+    set((const void*)k_zfwd<double, 2>); set((const void*)k_zfwd<float, 2>); set((const void*)k_zfwd<dfloat, 2>);
+    set((const void*)k_rows<double>); set((const void*)k_rows<float>); set((const void*)k_rows<dfloat>);
     set((const void*)k_rows_phys);
     return e;
 }

@@ -340,3 +340,17 @@ def test_prime_radix_axial_sizes(Nz):
         _check(c, s, h, 1e-10)
     finally:
         tc.tc_destroy(h)
+
+
+def test_minimum_sizes():
+    """The smallest accepted case: Nr = 9 (one interior compact row of each
+    kind), Ntheta = Nz = 4 (two azimuthal columns, padded 6 x 6)."""
+    cfg = dict(Nr=9, Ntheta=4, Nz=4, zeta=0.6, Re_i=100.0, Re_o=10.0, dt=2e-3)
+    v, e = inputs(9, 4, 4, 0.6, 3, "box", 5e-2, jmax=1, nmax=1)
+    c, s, h = _pair(cfg, v, e)
+    try:
+        tc.tc_step(h, 3)
+        s.step(3)
+        _check(c, s, h, 1e-10)
+    finally:
+        tc.tc_destroy(h)
