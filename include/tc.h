@@ -104,6 +104,14 @@ typedef struct {
     double Re_tau_inner;    /* u_tau h/nu with u_tau^2 = nu |W' - W/r| (Sec. 5) */
     double Re_tau_outer;
     double energy;          /* (1/2) <|u|^2> over the volume */
+    double dissipation;     /* nu <2 S:S>: viscous dissipation per unit volume,
+                               S the strain rate, radial derivatives by the
+                               compact first derivative (walls one-sided) */
+    double power_in;        /* work of the wall shear stress on the moving
+                               walls per unit volume:
+                               nu [R_o W_o (W'-W/r)(R_o) - R_i W_i (W'-W/r)(R_i)]
+                               / ((R_o^2 - R_i^2)/2); dE/dt = power_in -
+                               dissipation */
 } tc_stats;
 
 /* Create a case with the default box of Sec. 4, float64 precision and the
@@ -144,7 +152,9 @@ int tc_set_field(tc_handle* h, int which, const void* host_buf, size_t bytes);
 /* Bytes of one field in the given space. */
 size_t tc_field_bytes(const tc_handle* h, int which, int space);
 
-/* Torque, friction Reynolds numbers and kinetic energy of the current state. */
+/* Torque, friction Reynolds numbers, kinetic energy, viscous dissipation
+ * and wall power of the current state (synchronous on the handle's stream;
+ * uses the handle's transform scratch, so not while a step is in flight). */
 int tc_torque_stats(tc_handle* h, tc_stats* out);
 
 /* Launch stream (a cudaStream_t, or NULL for the legacy default stream). */

@@ -40,7 +40,8 @@ class tc_stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_longlong),
                 ("G_inner", ctypes.c_double), ("G_outer", ctypes.c_double),
                 ("Re_tau_inner", ctypes.c_double), ("Re_tau_outer", ctypes.c_double),
-                ("energy", ctypes.c_double)]
+                ("energy", ctypes.c_double), ("dissipation", ctypes.c_double),
+                ("power_in", ctypes.c_double)]
 
 
 class tc_result(ctypes.Structure):

@@ -486,9 +486,10 @@ int init_handle(tc_handle* h) {
     if ((rc_ = dalloc(h, pb, TC_NPROD * Z1))) return rc_;
     d.zbuf = zb; d.pbuf = pb;
     double* mean;
-    if ((rc_ = dalloc(h, mean, 5 * (size_t)d.Nr))) return rc_;
+    if ((rc_ = dalloc(h, mean, 6 * (size_t)d.Nr))) return rc_;
     d.U = mean; d.W = mean + d.Nr; d.HU = mean + 2 * d.Nr; d.HW = mean + 3 * d.Nr; d.eprof = mean + 4 * d.Nr;
-    CK(cudaMemset(mean, 0, 5 * (size_t)d.Nr * sizeof(double)));
+    d.dprof = mean + 5 * d.Nr;
+    CK(cudaMemset(mean, 0, 6 * (size_t)d.Nr * sizeof(double)));
     // circular Couette flow W = A r + B/r, W(R_i) = 1, W(R_o) = Re_o/Re_i
     {
         const double Ro = h->Ro, Wo = d.W_outer;
@@ -773,11 +774,13 @@ int tc_torque_stats(tc_handle* h, tc_stats* out) {
     if ((rc = ensure_init(h))) return rc;
     TcDev& d = h->d;
     const int N = d.Nr;
-    std::vector<double> W(N), ep(N);
+    std::vector<double> W(N), ep(N), dp(N);
     tc_launch_energy(d, h->stream);
+    tc_launch_strain(d, h->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(W.data(), d.W, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(ep.data(), d.eprof, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(dp.data(), d.dprof, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const double* e0 = &h->S.dwall[0];
     const double* e1 = &h->S.dwall[5];
@@ -793,7 +796,7 @@ int tc_torque_stats(tc_handle* h, tc_stats* out) {
     out->Re_tau_outer = std::sqrt(d.nu * so) / d.nu;
     // fourth-order radial quadrature with weight r (uniform grid):
     // trapezoid with end weights 3/8, 7/6, 23/24
-    double num = 0, den = 0;
+    double num = 0, dnum = 0, den = 0;
     const double hh = h->prm.stretch != 0.0 ? 2.0 / (N - 1) : (h->r[N - 1] - h->r[0]) / (N - 1);
     for (int j = 0; j < N; ++j) {
         double w = 1.0;
@@ -802,9 +805,16 @@ int tc_torque_stats(tc_handle* h, tc_stats* out) {
         else if (j == 2 || j == N - 3) w = 23.0 / 24.0;
         w *= hh * h->jac[j] * h->r[j];
         num += w * ep[j];
+        dnum += w * dp[j];
         den += w;
     }
     out->energy = 0.5 * num / den;
+    out->dissipation = d.nu * dnum / den;
+    // wall power: signed wall shear of the mean azimuthal flow times the
+    // wall velocity, over the volume per unit box area (R_o^2 - R_i^2)/2
+    const double Ri = h->r[0], Ro = h->r[N - 1];
+    const double ti = dWi - W[0] / Ri, to = dWo - W[N - 1] / Ro;
+    out->power_in = d.nu * (Ro * W[N - 1] * to - Ri * W[0] * ti) / (0.5 * (Ro * Ro - Ri * Ri));
     return TC_OK;
 }
 

@@ -99,8 +99,9 @@ struct TcDev {
 
     // physical output buffer for tc_get_field (float64 [Nr][Mz][Mt])
     double* phys;
-    // energy reduction output [Nr]
+    // energy and strain-rate reduction outputs [Nr]
     double* eprof;
+    double* dprof;
 
     int* flag;                  // device status flags: [0] non-finite, [1] pivot
 };
@@ -116,5 +117,8 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s);
 void tc_launch_init_state(const TcDev& d, cudaStream_t s);
 void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s);
 void tc_launch_energy(const TcDev& d, cudaStream_t s);
+// sum over Fourier slots of 2 S:S at every radial point -> d.dprof
+// (scratch: pbuf for the radial derivatives, zbuf for the densities)
+void tc_launch_strain(const TcDev& d, cudaStream_t s);
 cudaError_t tc_set_kernel_attributes();
 cudaError_t tc_set_line_kernel_attributes();

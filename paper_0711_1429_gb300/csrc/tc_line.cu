@@ -794,6 +794,115 @@ __global__ void __launch_bounds__(256) k_mean(TcDev d, int k, int init) {
 }
 
 // ---------------------------------------------------------------------------
+// Diagnostics: strain-rate density for the viscous dissipation.
+//
+// compact_D: first radial derivative of one Fourier slot of a field, the
+// operator of the energy budget: explicit one-sided 5-point D on the walls
+// (dwall) and on rows 1, Nr-2 (l1 rows with d0 = 1), compact rows
+// d0 . Df = l1 . f on 2..Nr-3 solved with the reversed factorisation dsol
+// (descending elimination, z kept in Df, then ascending substitution).
+__device__ void compact_D(const TcDev& d, const double2* __restrict__ f, double2* Df, int pair) {
+    const int N = d.Nr;
+    const size_t P = d.npairs;
+    auto F = [&](int i) { return f[(size_t)i * P + pair]; };
+    double2 D0 = cz(), D1 = cz(), DN2 = cz(), DN1 = cz();
+    for (int s = 0; s < 5; ++s) {
+        D0 = caxpy(D0, d.dwall[s], F(s));
+        DN1 = caxpy(DN1, d.dwall[5 + s], F(N - 5 + s));
+        D1 = caxpy(D1, d.l1[5 + s], F(d.start[1] + s));
+        DN2 = caxpy(DN2, d.l1[(N - 2) * 5 + s], F(d.start[N - 2] + s));
+    }
+    double2 z1 = cz(), z2 = cz();               // z_(jr+1), z_(jr+2)
+    for (int jr = N - 3; jr >= 2; --jr) {
+        const double* w0 = d.d0 + jr * 5;
+        const double* w1 = d.l1 + jr * 5;
+        double2 rhs = cz();
+        for (int s = 0; s < 5; ++s) {
+            const int c = jr - 2 + s;
+            rhs = caxpy(rhs, w1[s], F(c));
+            if (c == 0) rhs = caxpy(rhs, -w0[s], D0);
+            else if (c == 1) rhs = caxpy(rhs, -w0[s], D1);
+            else if (c == N - 2) rhs = caxpy(rhs, -w0[s], DN2);
+            else if (c == N - 1) rhs = caxpy(rhs, -w0[s], DN1);
+        }
+        const double* q = d.dsol + jr * 5;
+        const double2 z = caxpy(caxpy(rhs, -q[0], z2), -q[1], z1);
+        Df[(size_t)jr * P + pair] = z;
+        z2 = z1;
+        z1 = z;
+    }
+    double2 p1 = cz(), p2 = cz();               // Df_(i-1), Df_(i-2) among 2..Nr-3
+    for (int i = 2; i <= N - 3; ++i) {
+        const double* q = d.dsol + i * 5;
+        const double2 x = cscale(q[2], caxpy(caxpy(Df[(size_t)i * P + pair], -q[3], p1), -q[4], p2));
+        Df[(size_t)i * P + pair] = x;
+        p2 = p1;
+        p1 = x;
+    }
+    Df[pair] = D0;
+    Df[P + pair] = D1;
+    Df[(size_t)(N - 2) * P + pair] = DN2;
+    Df[(size_t)(N - 1) * P + pair] = DN1;
+}
+
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// One thread per Fourier slot (every slot; the (0,0) slot holds the mean
+// flow U, W): 2 S:S with the cylindrical strain components
+//   S_rr = Dv, S_tt = (i m/r) w + v/r, S_zz = i alpha u,
+//   S_rt = (Dw - w/r + (i m/r) v)/2, S_rz = (i alpha v + Du)/2,
+//   S_tz = ((i m/r) u + i alpha w)/2,
+// times the Parseval weight (1 for m = 0, 2 otherwise), into dens[r][slot].
+__global__ void __launch_bounds__(128) k_strain(TcDev d, double2* Du, double2* Dv, double2* Dw, double* dens) {
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pair >= d.npairs) return;
+    const int sl = pair / d.Nh, j = pair - sl * d.Nh;
+    const int n = sl < d.Nz / 2 ? sl : (sl == d.Nz / 2 ? 0 : sl - d.Nz);
+    const double m = j * d.m0, al = n * d.alpha0;
+    const double wgt = j == 0 ? 1.0 : 2.0;
+    compact_D(d, d.u, Du, pair);
+    compact_D(d, d.v, Dv, pair);
+    compact_D(d, d.w, Dw, pair);
+    const size_t P = d.npairs;
+    for (int i = 0; i < d.Nr; ++i) {
+        const size_t o = (size_t)i * P + pair;
+        const double ri = d.rinv[i];
+        const double2 U = d.u[o], V = d.v[o], W = d.w[o];
+        const double2 srr = Dv[o];
+        const double2 stt = caxpy(cimag(m * ri, W), ri, V);
+        const double2 szz = cimag(al, U);
+        const double2 srt = cscale(0.5, cadd(caxpy(Dw[o], -ri, W), cimag(m * ri, V)));
+        const double2 srz = cscale(0.5, cadd(cimag(al, V), Du[o]));
+        const double2 stz = cscale(0.5, cadd(cimag(m * ri, U), cimag(al, W)));
+        dens[o] = wgt * (2.0 * (cabs2(srr) + cabs2(stt) + cabs2(szz)) +
+                         4.0 * (cabs2(srt) + cabs2(srz) + cabs2(stz)));
+    }
+}
+
+// dprof[r] = sum over slots of dens[r][slot] (fixed order: reproducible)
+__global__ void __launch_bounds__(256) k_slot_sum(TcDev d, const double* __restrict__ dens) {
+    const int r = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < d.npairs; i += blockDim.x) acc += dens[(size_t)r * d.npairs + i];
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) d.dprof[r] = red[0];
+}
+
+void tc_launch_strain(const TcDev& d, cudaStream_t s) {
+    const size_t P1 = (size_t)d.Nr * d.npairs;   // <= Nr Mz Nh: fits the scratch
+    double2* D = reinterpret_cast<double2*>(d.pbuf);
+    double* dens = reinterpret_cast<double*>(d.zbuf);
+    k_strain<<<(d.npairs + 127) / 128, 128, 0, s>>>(d, D, D + P1, D + 2 * P1, dens);
+    k_slot_sum<<<d.Nr, 256, 0, s>>>(d, dens);
+}
+
+// ---------------------------------------------------------------------------
 void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
     k_setup<<<(d.npairs + 127) / 128, 128, 0, s>>>(d);
 }

@@ -155,7 +155,50 @@ def test_physical_field_and_stats_match_oracle():
         assert abs(st["G_inner"] - Gi) < 1e-10 * Gi and abs(st["G_outer"] - Go) < 1e-10 * Go
         assert abs(st["Re_tau_inner"] - ti) < 1e-10 * ti and abs(st["Re_tau_outer"] - to) < 1e-10 * to
         assert abs(st["energy"] - E) < 1e-10 * E
+        eps = dg.dissipation(c, s.S, u, vv, w)
+        Pin = dg.wall_power(c, s.S, s.W)
+        assert abs(st["dissipation"] - eps) < 1e-10 * eps
+        assert abs(st["power_in"] - Pin) < 1e-10 * abs(Pin)
         assert st["step"] == 3
+    finally:
+        tc.tc_destroy(h)
+
+
+@pytest.mark.parametrize("stretch", [0.0, 1.5])
+def test_dissipation_and_wall_power_match_oracle(stretch):
+    """eps and P_in of a perturbed state with a moving outer wall, on the
+    uniform and the stretched radial grid, several tiles of slots."""
+    cfg = dict(Nr=41, Ntheta=24, Nz=18, zeta=0.7, Re_i=300.0, Re_o=-60.0, dt=2e-3)
+    c = Case(41, 24, 18, 0.7, 300.0, -60.0, 2e-3, stretch=stretch)
+    s = OracleSolver(c)
+    v, e = inputs(41, 24, 18, 0.7, 21, "k2", 0.05)
+    s.set_fields(v=v, eta=e)
+    h = gpu_case(41, 24, 18, 0.7, 300.0, -60.0, 2e-3, v=v, eta=e, stretch=stretch)
+    try:
+        tc.tc_step(h, 2)
+        s.step(2)
+        u, vv, w = s.velocity()
+        st = tc.tc_torque_stats(h)
+        eps = dg.dissipation(c, s.S, u, vv, w)
+        Pin = dg.wall_power(c, s.S, s.W)
+        assert abs(st["dissipation"] - eps) < 1e-10 * eps, (st["dissipation"], eps)
+        assert abs(st["power_in"] - Pin) < 1e-10 * abs(Pin), (st["power_in"], Pin)
+    finally:
+        tc.tc_destroy(h)
+
+
+def test_laminar_dissipation_balances_wall_power():
+    """Circular Couette flow: eps = P_in = 2 nu B^2 (1/R_i^2 - 1/R_o^2)/V."""
+    h = gpu_case(65, 8, 8, 0.5, 100.0, -30.0, 1e-3)
+    try:
+        st = tc.tc_torque_stats(h)
+        c = Case(65, 8, 8, 0.5, 100.0, -30.0, 1e-3)
+        Ri, Ro, Wo = c.Ri, c.Ro, c.W_outer
+        A = (Wo * Ro - Ri) / (Ro * Ro - Ri * Ri)
+        B = Ri - A * Ri * Ri
+        exact = 2.0 * c.nu * B * B * (1.0 / Ri ** 2 - 1.0 / Ro ** 2) / (0.5 * (Ro * Ro - Ri * Ri))
+        assert abs(st["dissipation"] / exact - 1.0) < 1e-6
+        assert abs(st["power_in"] / exact - 1.0) < 2e-6
     finally:
         tc.tc_destroy(h)
 
