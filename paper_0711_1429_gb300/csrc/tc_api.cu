@@ -220,6 +220,41 @@ bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim, 
     return true;
 }
 
+// Tangent-form twiddles of a family-0 plan, per stage and jm: the twiddle
+// w_r = cos a + i sin a (a = -2 pi r jm/(Ns R)) is written k_r (1 + i tau_r)
+// with k_r = cos a, tau_r = sin a/cos a.  Entries per jm: R = 4: tau1 tau2
+// tau3 k1 k2 k3/k1; R = 3: tau1 tau2 k2/k1 k1 k1/2 k1 sin(2 pi/3);
+// R = 2: tau1 k1.  A cosine that vanishes is replaced by 1e-200 (the
+// products k_r u_r stay exact to rounding; |tau| <= 1e200).
+std::vector<double> tangent_twiddles(const FftPlan& p) {
+    const ld twopi = 6.283185307179586476925286766559005768L;
+    const ld s3 = 0.866025403784438646763723170752936183L;
+    std::vector<double> t;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.R[s], Ns = p.Ns[s];
+        for (int jm = 0; jm < Ns; ++jm) {
+            ld k[4] = {1, 1, 1, 1}, tau[4] = {0, 0, 0, 0};
+            for (int r = 1; r < R; ++r) {
+                const ld a = -twopi * (ld)(r * jm) / (ld)(Ns * R);
+                ld c = cosl(a);
+                if (fabsl(c) < 1e-200L) c = 1e-200L;
+                k[r] = c;
+                tau[r] = sinl(a) / c;
+            }
+            if (R == 4) {
+                for (ld x : {tau[1], tau[2], tau[3], k[1], k[2], k[3] / k[1]}) t.push_back((double)x);
+            } else if (R == 3) {
+                for (ld x : {tau[1], tau[2], k[2] / k[1], k[1], k[1] / 2, k[1] * s3}) t.push_back((double)x);
+            } else if (R == 2) {
+                for (ld x : {tau[1], k[1]}) t.push_back((double)x);
+            } else {
+                return {};   // family-0 plans have radices 2, 3, 4 only
+            }
+        }
+    }
+    return t;
+}
+
 bool is_2a3b(int n) {
     if (n < 1) return false;
     while (n % 2 == 0) n /= 2;
@@ -468,6 +503,12 @@ int init_handle(tc_handle* h) {
     if (twt_d.empty()) { twt_d.push_back(make_double2(1, 0)); twt_f.push_back(make_float2(1, 0)); }
     if ((rc_ = upload(h, d.twz_d, twz_d))) return rc_;
     if ((rc_ = upload(h, d.twt_d, twt_d))) return rc_;
+    {
+        std::vector<double> a = tangent_twiddles(d.pt), b = tangent_twiddles(d.ph);
+        if (a.empty() || b.empty()) { set_err("theta plan with a radix other than 2, 3, 4"); return TC_ERR_ARG; }
+        if ((rc_ = upload(h, d.twt_tan, a))) return rc_;
+        if ((rc_ = upload(h, d.twh_tan, b))) return rc_;
+    }
     if ((rc_ = upload(h, d.twz_f, twz_f))) return rc_;
     if ((rc_ = upload(h, d.twt_f, twt_f))) return rc_;
     // fields

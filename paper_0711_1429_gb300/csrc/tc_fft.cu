@@ -145,6 +145,57 @@ __device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int n
     for (int r = 0; r < R; ++r) dc[r * Ns] = v[dft_slot<R>(r)];
 }
 
+// Float64 Stockham butterfly of radix 2, 3 or 4 with the stage twiddles in
+// tangent form: w_r = k_r (1 + i tau_r), so v_r w_r = k_r u_r with
+// u_r = v_r (1 + i tau_r) (conjugate for the inverse), two fused
+// multiply-adds, and the factors k_r are carried by the multiply-adds of the
+// butterfly itself (k_3 = rho k_1 for radix 4, k_2 = rho k_1 for radix 3).
+// Radix 4 then takes 22 multiply-adds instead of 6 multiplies, 6
+// multiply-adds and 16 adds; radix 3 takes 16 instead of 22.  Table layout
+// per jm as built on the host (tangent_twiddles).
+template <int R> __host__ __device__ constexpr int tan_entries() { return R == 2 ? 2 : 6; }
+template <int R, int SIGN>
+__device__ __forceinline__ void stockham_bfly_tan(const double2* sc, double2* dcol, int j, int nb, int Ns,
+                                                  const double* __restrict__ tw) {
+    const int jm = j % Ns;
+    double2 v[R];
+    #pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sc[j + r * nb];
+    const double* t = tw + jm * tan_entries<R>();
+    auto tang = [](double2 a, double tau) {
+        const double s = SIGN < 0 ? tau : -tau;
+        return make_double2(fma(-s, a.y, a.x), fma(s, a.x, a.y));
+    };
+    double2* dc = dcol + (j / Ns) * Ns * R + jm;
+    if constexpr (R == 2) {
+        const double2 u1 = tang(v[1], t[0]);
+        const double k1 = t[1];
+        dc[0] = make_double2(fma(k1, u1.x, v[0].x), fma(k1, u1.y, v[0].y));
+        dc[Ns] = make_double2(fma(-k1, u1.x, v[0].x), fma(-k1, u1.y, v[0].y));
+    } else if constexpr (R == 3) {
+        const double2 u1 = tang(v[1], t[0]), u2 = tang(v[2], t[1]);
+        const double rho = t[2], k1 = t[3], hk = t[4], sk = SIGN < 0 ? t[5] : -t[5];
+        const double2 b = make_double2(fma(rho, u2.x, u1.x), fma(rho, u2.y, u1.y));
+        const double2 bm = make_double2(fma(-rho, u2.x, u1.x), fma(-rho, u2.y, u1.y));
+        const double2 t0 = make_double2(fma(-hk, b.x, v[0].x), fma(-hk, b.y, v[0].y));
+        dc[0] = make_double2(fma(k1, b.x, v[0].x), fma(k1, b.y, v[0].y));
+        dc[Ns] = make_double2(fma(sk, bm.y, t0.x), fma(-sk, bm.x, t0.y));
+        dc[2 * Ns] = make_double2(fma(-sk, bm.y, t0.x), fma(sk, bm.x, t0.y));
+    } else {
+        const double2 u1 = tang(v[1], t[0]), u2 = tang(v[2], t[1]), u3 = tang(v[3], t[2]);
+        const double k1 = t[3], k2 = t[4], rho = t[5];
+        const double ks = SIGN < 0 ? k1 : -k1;
+        const double2 a0 = make_double2(fma(k2, u2.x, v[0].x), fma(k2, u2.y, v[0].y));
+        const double2 a1 = make_double2(fma(-k2, u2.x, v[0].x), fma(-k2, u2.y, v[0].y));
+        const double2 b = make_double2(fma(rho, u3.x, u1.x), fma(rho, u3.y, u1.y));
+        const double2 bm = make_double2(fma(-rho, u3.x, u1.x), fma(-rho, u3.y, u1.y));
+        dc[0] = make_double2(fma(k1, b.x, a0.x), fma(k1, b.y, a0.y));
+        dc[2 * Ns] = make_double2(fma(-k1, b.x, a0.x), fma(-k1, b.y, a0.y));
+        dc[Ns] = make_double2(fma(ks, bm.y, a1.x), fma(-ks, bm.x, a1.y));
+        dc[3 * Ns] = make_double2(fma(-ks, bm.y, a1.x), fma(ks, bm.x, a1.y));
+    }
+}
+
 // Odd prime radix R (5, 7, 11, 13, 17).  With w = exp(SIGN 2 pi i/R) and
 // h = (R-1)/2, the inputs pair up as a_j = v_j + v_(R-j), b_j = v_j - v_(R-j)
 // (j = 1..h), and for k = 1..h
@@ -282,9 +333,16 @@ __host__ __device__ constexpr int plan_off_f(int M, int s, int F) {
     return o;
 }
 
+__host__ __device__ constexpr int plan_tan_off(int M, int s) {
+    int o = 0;
+    for (int i = 0; i < s; ++i) o += plan_ns_f(M, i, 0) * (plan_radix_f(M, i, 0) == 2 ? 2 : 6);
+    return o;
+}
+
 template <typename T, int SIGN, int M, int F, int S>
 __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t* src, typename V2<T>::t* dst,
-                                                              int ncols, const typename V2<T>::t* __restrict__ tw) {
+                                                              int ncols, const typename V2<T>::t* __restrict__ tw,
+                                                              const double* __restrict__ twtan) {
     typedef typename V2<T>::t C;
     if constexpr (S == plan_nst_f(M, F)) {
         return src;
@@ -296,10 +354,13 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
         for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
             const int col = b / nb;
             const int j = b - col * nb;
-            stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
+            if constexpr (std::is_same<T, double>::value && F == 0 && Ns > 1)
+                stockham_bfly_tan<R, SIGN>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S));
+            else
+                stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
         }
         __syncthreads();
-        return fft_fixed_stage<T, SIGN, M, F, S + 1>(dst, src, ncols, tw);
+        return fft_fixed_stage<T, SIGN, M, F, S + 1>(dst, src, ncols, tw, twtan);
     }
 }
 
@@ -307,8 +368,9 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
 // the supported grids, the run-time plan otherwise (same arithmetic).
 template <typename T, int SIGN, int F>
 __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
-                                  const FftPlan& pl, const typename V2<T>::t* __restrict__ tw) {
-#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0>(buf0, buf1, ncols, tw);
+                                  const FftPlan& pl, const typename V2<T>::t* __restrict__ tw,
+                                  const double* __restrict__ twtan = nullptr) {
+#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0>(buf0, buf1, ncols, tw, twtan);
     if constexpr (F == 2) {
         return fft_stockham<T, SIGN, 2>(buf0, buf1, ncols, pl, tw);
     } else {
@@ -433,8 +495,8 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         hA[k] = z;
     }
     __syncthreads();
-    C* r1 = fft<T, +1, 0>(fA, fB, 1, d.pt, twt<T>(d));
-    C* r2 = fft<T, +1, 0>(hA, hB, 1, d.ph, twh<T>(d));
+    C* r1 = fft<T, +1, 0>(fA, fB, 1, d.pt, twt<T>(d), d.twt_tan);
+    C* r2 = fft<T, +1, 0>(hA, hB, 1, d.ph, twh<T>(d), d.twh_tan);
     C* o1 = (r1 == fA) ? fB : fA;
     C* o2 = (r2 == hA) ? hB : hA;
     for (int m = threadIdx.x; m < H; m += blockDim.x) {
@@ -454,8 +516,8 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         o2[m] = z;
     }
     __syncthreads();
-    C* out = fft<T, -1, 0>(o1, r1, 2, d.pt, twt<T>(d));
-    C* out2 = fft<T, -1, 0>(o2, r2, 1, d.ph, twh<T>(d));
+    C* out = fft<T, -1, 0>(o1, r1, 2, d.pt, twt<T>(d), d.twt_tan);
+    C* out2 = fft<T, -1, 0>(o2, r2, 1, d.ph, twh<T>(d), d.twh_tan);
     C* pb = reinterpret_cast<C*>(d.pbuf);
     for (int idx = threadIdx.x; idx < 3 * Nh; idx += blockDim.x) {
         const int c = idx / Nh, j = idx - c * Nh;

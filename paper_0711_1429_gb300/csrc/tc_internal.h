@@ -85,6 +85,10 @@ struct TcDev {
     const double2* twz_d;
     const double2* twt_d;
     const double2* twh_d;
+    // theta-row twiddles in tangent form for the float64 radix-2/3/4 stages
+    // (per stage and jm: tau_r = sin/cos, the cosines and their ratios)
+    const double* twt_tan;
+    const double* twh_tan;
     const double2* twr_d;
     const float2* twz_f;
     const float2* twt_f;
