@@ -503,6 +503,19 @@ int init_handle(tc_handle* h) {
     if (twt_d.empty()) { twt_d.push_back(make_double2(1, 0)); twt_f.push_back(make_float2(1, 0)); }
     if ((rc_ = upload(h, d.twz_d, twz_d))) return rc_;
     if ((rc_ = upload(h, d.twt_d, twt_d))) return rc_;
+    // float64 z transforms in the radix-3/4/2 plan with tangent twiddles
+    // when the padded axial length has a compile-time plan
+    d.zfam0 = 0;
+    if (tc_fft_fixed_length(d.Mz) && is_2a3b(d.Mz)) {
+        std::vector<ld> r0, i0;
+        if (make_plan(d.Mz, d.pz0, r0, i0, 0)) {
+            std::vector<double> c = tangent_twiddles(d.pz0);
+            if (!c.empty()) {
+                if ((rc_ = upload(h, d.twz_tan, c))) return rc_;
+                d.zfam0 = 1;
+            }
+        }
+    }
     {
         std::vector<double> a = tangent_twiddles(d.pt), b = tangent_twiddles(d.ph);
         if (a.empty() || b.empty()) { set_err("theta plan with a radix other than 2, 3, 4"); return TC_ERR_ARG; }

@@ -364,8 +364,15 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
     }
 }
 
+bool tc_fft_fixed_length(int M) {
+    for (int m : {12, 18, 24, 36, 48, 72, 96, 144, 192, 288, 384, 576, 768, 1152, 1536})
+        if (M == m) return true;
+    return false;
+}
+
 // Dispatch on the transform length: compile-time plans for the lengths of
-// the supported grids, the run-time plan otherwise (same arithmetic).
+// the supported grids (those of tc_fft_fixed_length), the run-time plan
+// otherwise (same arithmetic).
 template <typename T, int SIGN, int F>
 __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw,
@@ -403,7 +410,9 @@ template <> __device__ __forceinline__ const float2* twr<float>(const TcDev& d) 
 
 
 // ---- k_zinv: spectral (u, v, w) -> zbuf[f][r][q][j] ---------------------------
-// ZF = 1: axial lengths 2^a 3^b; ZF = 2: lengths with odd prime factors.
+// ZF = 0: float64 with the radix-3/4/2 plan pz0 and tangent-form twiddles
+// (compile-time lengths only); ZF = 1: axial lengths 2^a 3^b; ZF = 2:
+// lengths with odd prime factors.
 template <typename T, int ZF>
 __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict__ f0,
                                               const double2* __restrict__ f1,
@@ -431,7 +440,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1, ZF>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, +1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz<T>(d), d.twz_tan);
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
@@ -562,7 +571,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
-    C* res = fft<T, -1, ZF>(buf0, buf1, ct, d.pz, twz<T>(d));
+    C* res = fft<T, -1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz<T>(d), d.twz_tan);
     T scale;
     if constexpr (std::is_same<T, double>::value) scale = d.fscale;
     else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;
@@ -640,13 +649,16 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
     const size_t smr = 5 * (size_t)d.Mt * sizeof(C);   // 2 x (2 full + 1 half) columns
     const bool odd = z_has_odd_primes(d);
+    const bool tan = std::is_same<T, double>::value && d.zfam0;
     if (which == 0) {
         if (odd) k_zinv<T, 2><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
+        else if (tan) k_zinv<double, 0><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
         else k_zinv<T, 1><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
     } else if (which == 1) {
         k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
     } else {
         if (odd) k_zfwd<T, 2><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
+        else if (tan) k_zfwd<double, 0><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
         else k_zfwd<T, 1><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
     }
 }
@@ -667,6 +679,7 @@ void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s)
     TcDev dd = d;
     // one field through slot 0 of zbuf (always float64 here)
     if (z_has_odd_primes(d)) k_zinv<double, 2><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
+    else if (d.zfam0) k_zinv<double, 0><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
     else k_zinv<double, 1><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
     k_rows_phys<<<dim3(d.Mz, d.Nr), 256, 2 * (size_t)d.Mt * sizeof(double2), s>>>(dd);
 }
@@ -685,6 +698,7 @@ cudaError_t tc_set_kernel_attributes() {
     set((const void*)k_zfwd<double, 1>); set((const void*)k_zfwd<float, 1>); set((const void*)k_zfwd<dfloat, 1>);
     set((const void*)k_zfwd<double, 2>); set((const void*)k_zfwd<float, 2>); set((const void*)k_zfwd<dfloat, 2>);
     set((const void*)k_rows<double>); set((const void*)k_rows<float>); set((const void*)k_rows<dfloat>);
+    set((const void*)k_zinv<double, 0>); set((const void*)k_zfwd<double, 0>);
     set((const void*)k_rows_phys);
     return e;
 }

@@ -82,6 +82,11 @@ struct TcDev {
     // (Mt), ph (Mt/2, the real transforms of one signal) and twr[k] =
     // exp(-2 pi i k/Mt), k < Mt/2, for their pre/post-processing.
     FftPlan pz, pt, ph;
+    // float64 z transforms with the theta-row plan family (radix 3, 4, 2 in
+    // tangent form) when Mz has a compile-time plan: zfam0 = 1, plan pz0
+    int zfam0;
+    FftPlan pz0;
+    const double* twz_tan;
     const double2* twz_d;
     const double2* twt_d;
     const double2* twh_d;
@@ -121,6 +126,8 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s);
 void tc_launch_init_state(const TcDev& d, cudaStream_t s);
 void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s);
 void tc_launch_energy(const TcDev& d, cudaStream_t s);
+// transform lengths with a compile-time plan in the FFT kernels
+bool tc_fft_fixed_length(int M);
 // sum over Fourier slots of 2 S:S at every radial point -> d.dprof
 // (scratch: pbuf for the radial derivatives, zbuf for the densities)
 void tc_launch_strain(const TcDev& d, cudaStream_t s);
