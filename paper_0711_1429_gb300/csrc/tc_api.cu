@@ -559,7 +559,7 @@ int init_handle(tc_handle* h) {
     if ((rc_ = dalloc(h, d.tab_lv, (size_t)d.Nr * 5 * d.npairs))) return rc_;
     if ((rc_ = dalloc(h, d.tab_c, (size_t)d.Nr * d.npairs))) return rc_;
     if ((rc_ = dalloc(h, d.tab_c1, (size_t)d.Nr * d.npairs))) return rc_;
-    if (d.prec == TC_PREC_DF64) {
+    if (d.prec != TC_PREC_FP64) {     // float (hi, lo) copies of c and c'
         if ((rc_ = dalloc(h, d.tab_cx, (size_t)d.Nr * d.npairs))) return rc_;
         if ((rc_ = dalloc(h, d.tab_c1x, (size_t)d.Nr * d.npairs))) return rc_;
     }

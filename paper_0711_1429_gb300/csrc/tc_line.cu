@@ -50,10 +50,14 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 // (i s) * a
 __device__ __forceinline__ double2 cimag(double s, double2 a) { return make_double2(-s * a.y, s * a.x); }
+// i * a
+__device__ __forceinline__ double2 ci(double2 a) { return make_double2(-a.y, a.x); }
 // a + s * b
 __device__ __forceinline__ double2 caxpy(double2 a, double s, double2 b) { return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y)); }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+// finiteness from the exponent bits (integer pipe, no float64 compare)
+__device__ __forceinline__ bool dfinite(double x) { return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ bool cfinite(double2 a) { return dfinite(a.x) && dfinite(a.y); }
 
 __device__ __forceinline__ double2 ld_prod(const double2* p, size_t o) { return p[o]; }
 __device__ __forceinline__ double2 ld_prod(const float2* p, size_t o) { float2 f = p[o]; return make_double2(f.x, f.y); }
@@ -324,8 +328,10 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
         const double2 V = d.v[(size_t)i * P + pair];
         const double2 E = d.eta[(size_t)i * P + pair];
         const double2 Dsv = caxpy(Dv, ri, V);
-        const double2 uu = cscale(c, csub(cimag(al, Dsv), cimag(m * ri, E)));
-        const double2 ww = cscale(c, cadd(cimag(m * ri, Dsv), cimag(al, E)));
+        // u = i (c alpha Dsv - c m/r eta), w = i (c m/r Dsv + c alpha eta)
+        const double ca = c * al, cm = c * m * ri;
+        const double2 uu = ci(make_double2(fma(ca, Dsv.x, -cm * E.x), fma(ca, Dsv.y, -cm * E.y)));
+        const double2 ww = ci(make_double2(fma(cm, Dsv.x, ca * E.x), fma(cm, Dsv.y, ca * E.y)));
         d.u[(size_t)i * P + pair] = uu;
         d.w[(size_t)i * P + pair] = ww;
         if (partner >= 0) {
@@ -356,6 +362,41 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 // explicit rows are formed in double-float arithmetic (float32 pipe) from the
 // double-float products; the right sides, the solves, the RK memory and the
 // reconstruction are float64 in every form.
+// Inner functions of the explicit rows at one radial point, from the five
+// products and u, v, w: A, B, C of the v rows (C without the continuity
+// term) and A, B of the eta rows, as listed above.
+template <typename T, typename CT>
+__device__ __forceinline__ void inner_terms(const CT& pa, const CT& uv, const CT& uw, const CT& vw, const CT& pb,
+                                            const CT& U, const CT& V, const CT& W, T ri, T c, T c1,
+                                            T mt, T at, T nut, CT& a, CT& b, CT& cc, CT& ae, CT& be) {
+    const T ri2 = ri * ri;
+    // v rows
+    a = timag(-at, uv);
+    a = tadd(a, timag(-mt * ri, vw));
+    a = taxpy(a, ri, pb);
+    a = tadd(a, timag((T)-2 * nut * mt * ri2, W));
+    b = timag(at * c1, uv);
+    b = tadd(b, timag(-mt * ((T)2 * c * ri2 - c1 * ri), vw));
+    b = taxpy(b, c * at * at, pa);
+    b = taxpy(b, c * (T)2 * at * mt * ri, uw);
+    b = taxpy(b, c * mt * mt * ri2, pb);
+    b = tadd(b, timag((T)-2 * nut * mt * c1 * ri2, W));
+    cc = timag(-at * c, uv);
+    cc = tadd(cc, timag(-mt * c * ri, vw));
+    cc = tadd(cc, timag((T)2 * nut * mt * c * ri2, W));
+    // eta rows
+    ae = tscale(mt * at * ri, pa);
+    ae = tadd(ae, timag((T)-2 * mt * ri2, uv));
+    ae = taxpy(ae, mt * mt * ri2 - at * at, uw);
+    ae = taxpy(ae, -at * mt * ri, pb);
+    ae = tadd(ae, timag((T)2 * at * ri, vw));
+    ae = tadd(ae, timag((T)4 * nut * mt * ri2 * ri, U));
+    ae = taxpy(ae, (T)2 * nut * mt * at * ri2, V);
+    be = timag(-mt * ri, uv);
+    be = tadd(be, timag(at, vw));
+    be = tadd(be, timag((T)2 * nut * mt * ri2, U));
+}
+
 template <int MODE, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
     constexpr bool MIXED = (MODE == 1);
@@ -459,24 +500,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
             const CT U = from_d2<CT>(Ud), V = from_d2<CT>(Vd), W = from_d2<CT>(Wd);
             T ri, c, c1;
             double c1d = 0.0;
-            if constexpr (MODE == 1) { ri = d.rinvf[i]; c = (T)d.tab_c[o]; c1d = d.tab_c1[o]; c1 = (T)c1d; }
+            if constexpr (MODE == 1) { ri = d.rinvf[i]; c = d.tab_cx[o].x; c1d = d.tab_c1[o]; c1 = d.tab_c1x[o].x; }
             else if constexpr (MODE == 2) { ri = as_df(d.rinvx[i]); c = as_df(d.tab_cx[o]); c1 = as_df(d.tab_c1x[o]); }
             else { ri = d.rinv[i]; c = d.tab_c[o]; c1d = d.tab_c1[o]; c1 = c1d; }
-            const T ri2 = ri * ri;
-            // v rows
-            CT a = timag(-at, uv);
-            a = tadd(a, timag(-mt * ri, vw));
-            a = taxpy(a, ri, pb);
-            a = tadd(a, timag((T)-2 * nut * mt * ri2, W));
-            CT b = timag(at * c1, uv);
-            b = tadd(b, timag(-mt * ((T)2 * c * ri2 - c1 * ri), vw));
-            b = taxpy(b, c * at * at, pa);
-            b = taxpy(b, c * (T)2 * at * mt * ri, uw);
-            b = taxpy(b, c * mt * mt * ri2, pb);
-            b = tadd(b, timag((T)-2 * nut * mt * c1 * ri2, W));
-            CT cc = timag(-at * c, uv);
-            cc = tadd(cc, timag(-mt * c * ri, vw));
-            cc = tadd(cc, timag((T)2 * nut * mt * c * ri2, W));
+            CT a, b, cc, ae, be;
+            inner_terms(pa, uv, uw, vw, pb, U, V, W, ri, c, c1, mt, at, nut, a, b, cc, ae, be);
             if constexpr (MODE == 1) {
                 const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
                 Cp[4] = cscale(c1d, phi);
@@ -488,17 +516,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
                 cc = caxpy(cc, -3.0 * nu * c1d, phi);
             }
             Av[4] = a; Bv[4] = b; Cv[4] = cc;
-            // eta rows
-            CT ae = tscale(mt * at * ri, pa);
-            ae = tadd(ae, timag((T)-2 * mt * ri2, uv));
-            ae = taxpy(ae, mt * mt * ri2 - at * at, uw);
-            ae = taxpy(ae, -at * mt * ri, pb);
-            ae = tadd(ae, timag((T)2 * at * ri, vw));
-            ae = tadd(ae, timag((T)4 * nut * mt * ri2 * ri, U));
-            ae = taxpy(ae, (T)2 * nut * mt * at * ri2, V);
-            CT be = timag(-mt * ri, uv);
-            be = tadd(be, timag(at, vw));
-            be = tadd(be, timag((T)2 * nut * mt * ri2, U));
             Ae[4] = ae; Be[4] = be;
         }
         if (i < 4) continue;
@@ -535,6 +552,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
     xw[0] = cz(); ew[0] = cz(); k2w[0] = k2N;
     d.v[(size_t)(N - 1) * P + pair] = cz();
     d.eta[(size_t)(N - 1) * P + pair] = cz();
+    const double hdtnu = hdt * nu;
     auto h_update = [&](int jr, bool do_v, bool do_e) {
         const size_t o = (size_t)jr * P + pair;
         if (do_v) {
@@ -545,8 +563,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
         if (do_e) {
             double2 acc = cz();
             for (int s = 0; s < 5; ++s)
-                acc = caxpy(acc, nu * (d.l2[jr * 5 + s] - d.d0[jr * 5 + s] * k2w[s]), ew[s]);
-            d.He[o] = caxpy(d.He[o], hdt, acc);
+                acc = caxpy(acc, fma(-d.d0[jr * 5 + s], k2w[s], d.l2[jr * 5 + s]), ew[s]);
+            d.He[o] = caxpy(d.He[o], hdtnu, acc);
         }
     };
     for (int i = N - 2; i >= 0; --i) {
