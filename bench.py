@@ -16,6 +16,7 @@ shard across GPUs here: "replicas only"); value = all ranks' grid-point
 steps / max over ranks of the timed region.
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -354,7 +355,7 @@ def run_gpu(args):
             stats = tc.tc_torque_stats(h)
         wall = dist.max(time.perf_counter() - t0)
         e2e = {"value": gp * args.e2e_steps * world / wall, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + 7 * 8,
+               "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + ctypes.sizeof(tc.tc_stats),
                "steps": args.e2e_steps, "torque_inner": stats["G_inner"]}
     device_bytes = tc.tc_device_bytes(h)
     tc.tc_destroy(h)

@@ -799,23 +799,9 @@ int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
     if (bytes != need) { set_err("buffer size " + std::to_string(bytes) + " != " + std::to_string(need)); return TC_ERR_SIZE; }
     double2* dst = which == TC_FIELD_V ? d.v : d.eta;
     CK(cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, h->stream));
-    // Hermitian m = 0 column, zero Nyquist slot and (0,0): small fix-up copies
-    // (2 (Nz/2 - 1) + Nh + 1 elements per radial point) done on the device.
-    std::vector<double2> col((size_t)d.Nr * d.Nz);
-    const double2* hb = static_cast<const double2*>(buf);
-    for (int r = 0; r < d.Nr; ++r)
-        for (int s = 0; s < d.Nz; ++s) col[(size_t)r * d.Nz + s] = hb[((size_t)r * d.Nz + s) * d.Nh];
-    for (int r = 0; r < d.Nr; ++r) {
-        double2* c = &col[(size_t)r * d.Nz];
-        c[0] = make_double2(0.0, 0.0);
-        c[d.Nz / 2] = make_double2(0.0, 0.0);
-        for (int n = 1; n < d.Nz / 2; ++n) c[d.Nz - n] = make_double2(c[n].x, -c[n].y);
-    }
-    CK(cudaMemcpy2DAsync(dst, d.Nh * sizeof(double2), col.data(), sizeof(double2), sizeof(double2),
-                         (size_t)d.Nr * d.Nz, cudaMemcpyHostToDevice, h->stream));
-    std::vector<double2> zero((size_t)d.Nr * d.Nh, make_double2(0.0, 0.0));
-    CK(cudaMemcpy2DAsync(dst + (size_t)(d.Nz / 2) * d.Nh, (size_t)d.npairs * sizeof(double2), zero.data(),
-                         d.Nh * sizeof(double2), d.Nh * sizeof(double2), d.Nr, cudaMemcpyHostToDevice, h->stream));
+    // Hermitian m = 0 column, zero Nyquist slot and (0,0), on the device
+    tc_launch_realify(d, dst, h->stream);
+    CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     h->need_init = true;
     h->phase = 0;

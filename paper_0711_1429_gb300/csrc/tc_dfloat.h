@@ -77,3 +77,63 @@ __device__ __forceinline__ dfloat df_dot2(dfloat a, dfloat b, dfloat c, dfloat d
     fast_two_sum(s, e, h, l);
     return dfloat(h, l);
 }
+
+// a + s*b with one renormalisation
+__device__ __forceinline__ dfloat df_fma(dfloat a, dfloat s, dfloat b) {
+    const float ph = s.hi * b.hi;
+    float pe = fmaf(s.hi, b.hi, -ph);
+    pe = fmaf(s.hi, b.lo, pe);
+    pe = fmaf(s.lo, b.hi, pe);
+    float t, f;
+    two_sum(a.hi, ph, t, f);
+    f += pe + a.lo;
+    float h, l;
+    fast_two_sum(t, f, h, l);
+    return dfloat(h, l);
+}
+
+// ---- float64 <-> float32 / double-float by integer operations ---------------
+// GB300's float64 pipe also executes the float64 <-> float32 conversions, so
+// the float32 and double-float kernels move values in and out of float64
+// storage with bit manipulation (integer selects only):
+//   f_bits:  the leading 24 significand bits of x as a float (truncated);
+//   df_bits: hi = f_bits(x), lo = the next 23 bits, made a float exactly as
+//            (2^23 + n) - 2^23 and scaled (x = hi + lo to 2^-46 relative);
+//   d_bits:  exact widening of a float,
+//   d_of:    d_bits(hi) + d_bits(lo), one exact float64 add.
+// |x| < 2^-126 gives 0 (subnormal floats become 0), |x| >= 2^128 infinity,
+// NaN stays NaN.
+__device__ __forceinline__ unsigned f_bits_u(unsigned h32, unsigned l32) {
+    const unsigned sgn = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7ffu);
+    const int fe = e - 1023 + 127;
+    const unsigned hm = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+    return fe >= 1 && fe <= 254 ? (sgn | ((unsigned)fe << 23) | hm)
+         : fe <= 0 ? sgn
+         : (sgn | 0x7f800000u | (e == 0x7ff && (hm | (l32 & 0x1fffffffu)) ? 0x400000u : 0u));
+}
+__device__ __forceinline__ float f_bits(double x) {
+    return __uint_as_float(f_bits_u((unsigned)__double2hiint(x), (unsigned)__double2loint(x)));
+}
+__device__ __forceinline__ dfloat df_bits(double x) {
+    const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
+    const unsigned sgn = h32 & 0x80000000u;
+    const int e = (int)((h32 >> 20) & 0x7ffu);
+    const int fe = e - 1023 + 127;
+    const float n = __uint_as_float(0x4b000000u | ((l32 & 0x1fffffffu) >> 6)) - 8388608.0f;
+    const int le = e - 1069 + 127;                     // exponent of 2^(e - 1069)
+    const float sc = __uint_as_float(le >= 1 ? (unsigned)le << 23 : 0u);
+    const unsigned lb = fe >= 1 && fe <= 254 ? (__float_as_uint(n * sc) | sgn) : sgn;
+    return dfloat(__uint_as_float(f_bits_u(h32, l32)), __uint_as_float(lb));
+}
+__device__ __forceinline__ double d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sgn = u & 0x80000000u;
+    const unsigned fe = (u >> 23) & 0xffu, fm = u & 0x7fffffu;
+    const unsigned hi = fe == 0 ? sgn
+                      : fe == 0xff ? (sgn | 0x7ff00000u | (fm ? 0x80000u : 0u))
+                      : (sgn | ((fe + 1023 - 127) << 20) | (fm >> 3));
+    const unsigned lo = (fe == 0 || fe == 0xff) ? 0u : (fm << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double d_of(dfloat a) { return d_bits(a.hi) + d_bits(a.lo); }

@@ -25,6 +25,13 @@
 #include "tc_dfloat.h"
 #include <type_traits>
 
+// float64 state -> arithmetic type of the transform; float and double-float
+// through integer bit operations (the float64 pipe also does conversions)
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return f_bits(x); }
+template <> __device__ __forceinline__ dfloat from_f64<dfloat>(double x) { return df_bits(x); }
+
 template <typename T> struct V2;
 template <> struct V2<double> { typedef double2 t; };
 template <> struct V2<float> { typedef float2 t; };
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         C val; val.x = 0; val.y = 0;
         if (s >= 0) {
             double2 x = src[((size_t)r * Nz + s) * Nh + j0 + c];
-            val.x = (T)x.x; val.y = (T)x.y;
+            val.x = from_f64<T>(x.x); val.y = from_f64<T>(x.y);
         }
         buf0[c * Mz + q] = val;
     }

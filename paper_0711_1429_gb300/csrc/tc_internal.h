@@ -124,6 +124,8 @@ void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s);
 void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s);
 void tc_launch_setup_tables(const TcDev& d, cudaStream_t s);
 void tc_launch_init_state(const TcDev& d, cudaStream_t s);
+// zero the (0,0) and Nyquist slots and make the m = 0 column Hermitian
+void tc_launch_realify(const TcDev& d, double2* field, cudaStream_t s);
 void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s);
 void tc_launch_energy(const TcDev& d, cudaStream_t s);
 // transform lengths with a compile-time plan in the FFT kernels

@@ -60,7 +60,7 @@ __device__ __forceinline__ bool dfinite(double x) { return (__double2hiint(x) & 
 __device__ __forceinline__ bool cfinite(double2 a) { return dfinite(a.x) && dfinite(a.y); }
 
 __device__ __forceinline__ double2 ld_prod(const double2* p, size_t o) { return p[o]; }
-__device__ __forceinline__ double2 ld_prod(const float2* p, size_t o) { float2 f = p[o]; return make_double2(f.x, f.y); }
+__device__ __forceinline__ double2 ld_prod(const float2* p, size_t o) { float2 f = p[o]; return make_double2(d_bits(f.x), d_bits(f.y)); }
 
 // generic complex helpers for float2 / double2
 template <typename CT> __device__ __forceinline__ CT tz() { CT r; r.x = 0; r.y = 0; return r; }
@@ -69,12 +69,36 @@ template <typename CT> __device__ __forceinline__ CT tadd(CT a, CT b) { CT r; r.
 template <typename CT, typename T> __device__ __forceinline__ CT taxpy(CT a, T s, CT b) { CT r; r.x = fma(s, b.x, a.x); r.y = fma(s, b.y, a.y); return r; }
 template <typename CT, typename T> __device__ __forceinline__ CT tscale(T s, CT a) { CT r; r.x = s * a.x; r.y = s * a.y; return r; }
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
-__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+// float32 <-> float64 through the integer conversions of tc_dfloat.h (the
+// float64 pipe is the mixed line kernel's bottleneck); the double-float form
+// converts with float64 instructions, which measured faster there (fewer
+// registers in a kernel that is already at its register budget)
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(d_bits(a.x), d_bits(a.y)); }
 __device__ __forceinline__ double2 to_d2(dcomplex a) { return make_double2((double)a.x, (double)a.y); }
 template <typename CT> __device__ __forceinline__ CT from_d2(double2 a);
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
-template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2(f_bits(a.x), f_bits(a.y)); }
 template <> __device__ __forceinline__ dcomplex from_d2<dcomplex>(double2 a) { dcomplex r; r.x = dfloat(a.x); r.y = dfloat(a.y); return r; }
+__device__ __forceinline__ dcomplex dc_bits(double2 a) { dcomplex r; r.x = df_bits(a.x); r.y = df_bits(a.y); return r; }
+__device__ __forceinline__ dcomplex dc_fma(const dcomplex& a, dfloat s, const dcomplex& b) {
+    dcomplex r;
+    r.x = df_fma(a.x, s, b.x);
+    r.y = df_fma(a.y, s, b.y);
+    return r;
+}
+__device__ __forceinline__ dcomplex dc_scale(dfloat s, const dcomplex& a) {
+    dcomplex r;
+    r.x = s * a.x;
+    r.y = s * a.y;
+    return r;
+}
+__device__ __forceinline__ dcomplex dc_i(const dcomplex& a) {   // i a
+    dcomplex r;
+    r.x = -a.y;
+    r.y = a.x;
+    return r;
+}
+__device__ __forceinline__ dcomplex dc_of(float2 a) { dcomplex r; r.x = dfloat(a.x, 0.0f); r.y = dfloat(a.y, 0.0f); return r; }
 __device__ __forceinline__ double2 ld_prod(const dcomplex* p, size_t o) { return to_d2(p[o]); }
 __device__ __forceinline__ dfloat as_df(float2 v) { return dfloat(v.x, v.y); }
 
@@ -417,6 +441,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
     const double hdt = (d.rk_beta[k] + d.rk_alpha[kn]) * d.dt;
     const double nu = d.nu;
     const T mt = (T)m, at = (T)al, nut = (T)nu;
+    // double-float constants of the mixed form's continuity term
+    const dfloat mD(m), alD(al), m3nu(-3.0 * nu);
+    const dfloat* l2x = reinterpret_cast<const dfloat*>(d.l2x);
+    const dfloat* rinvx = reinterpret_cast<const dfloat*>(d.rinvx);
     const T* w0s;
     const T* w1s;
     const T* w2s;
@@ -429,11 +457,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
 
     // ---- forward sweep: explicit rows, right sides, forward elimination ----
     CT Av[5], Bv[5], Cv[5], Ae[5], Be[5];
-    double2 Cp[5];                              // continuity inner function (mixed form)
-    for (int s = 0; s < 5; ++s) {
-        Av[s] = Bv[s] = Cv[s] = Ae[s] = Be[s] = tz<CT>();
-        Cp[s] = cz();
-    }
+    dcomplex Cp[5];                             // continuity inner function (mixed form)
+    for (int s = 0; s < 5; ++s) Av[s] = Bv[s] = Cv[s] = Ae[s] = Be[s] = tz<CT>();
     double2 yv1 = cz(), yv2 = cz(), ye1 = cz(), ye2 = cz();   // y_{j-1}, y_{j-2}
     double2 rv_prev = cz(), re_prev = cz(), re_row1 = cz();
     const double fv = TAB(d.tab_luv, k, 0, 0), gv = TAB(d.tab_luv, k, N - 1, 0);
@@ -454,11 +479,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
             acc = taxpy(acc, w1s[j * 5 + s], Bv[s]);
             acc = taxpy(acc, w2s[j * 5 + s], Cv[s]);
         }
-        double2 r = to_d2(acc);
+        double2 r;
         if constexpr (MIXED) {
-            double2 cc = cz();
-            for (int s = 0; s < 5; ++s) cc = caxpy(cc, d.l2[j * 5 + s], Cp[s]);
-            r = caxpy(r, -3.0 * nu, cc);
+            // float32 rows plus the continuity term -3 nu l2 . (c' phi) in
+            // double-float, then widened to float64
+            dcomplex cc;
+            for (int s = 0; s < 5; ++s) cc = dc_fma(cc, l2x[j * 5 + s], Cp[s]);
+            r = to_d2(dc_fma(dc_of(acc), m3nu, cc));
+        } else {
+            r = to_d2(acc);
         }
         return r;
     };
@@ -500,14 +529,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
             const CT U = from_d2<CT>(Ud), V = from_d2<CT>(Vd), W = from_d2<CT>(Wd);
             T ri, c, c1;
             double c1d = 0.0;
-            if constexpr (MODE == 1) { ri = d.rinvf[i]; c = d.tab_cx[o].x; c1d = d.tab_c1[o]; c1 = d.tab_c1x[o].x; }
+            if constexpr (MODE == 1) { ri = d.rinvf[i]; c = d.tab_cx[o].x; c1 = d.tab_c1x[o].x; }
             else if constexpr (MODE == 2) { ri = as_df(d.rinvx[i]); c = as_df(d.tab_cx[o]); c1 = as_df(d.tab_c1x[o]); }
             else { ri = d.rinv[i]; c = d.tab_c[o]; c1d = d.tab_c1[o]; c1 = c1d; }
             CT a, b, cc, ae, be;
             inner_terms(pa, uv, uw, vw, pb, U, V, W, ri, c, c1, mt, at, nut, a, b, cc, ae, be);
             if constexpr (MODE == 1) {
-                const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
-                Cp[4] = cscale(c1d, phi);
+                // phi = i alpha u + (i m/r) w, times c', in double-float
+                const dcomplex phi = dc_i(dc_fma(dc_scale(alD, dc_bits(Ud)), mD * rinvx[i], dc_bits(Wd)));
+                Cp[4] = dc_scale(as_df(d.tab_c1x[o]), phi);
             } else if constexpr (MODE == 2) {
                 const CT phi = tadd(timag(at, U), timag(mt * ri, W));
                 cc = taxpy(cc, (T)(-3.0 * nu) * c1, phi);
@@ -617,20 +647,21 @@ __global__ void __launch_bounds__(128) k_init(TcDev d) {
         const size_t o = (size_t)j * P + pair;
         double2 hv = cz(), he = cz();
         if (j >= 2 && j <= N - 3) {
-            double M5[5], L5[5];
-            v_band(d, j, m, al, M5, L5);
+            // mass band M = d0 - l2 c + l1 c' from the c, c' tables, implicit
+            // band L from the table of k_setup
             for (int s = 0; s < 5; ++s) {
-                const double2 x = d.v[(size_t)(j - 2 + s) * P + pair];
-                hv = caxpy(hv, M5[s] + adt * L5[s], x);
+                const size_t oi = (size_t)(j - 2 + s) * P + pair;
+                const double M5 = d.d0[j * 5 + s] - d.l2[j * 5 + s] * d.tab_c[oi] + d.l1[j * 5 + s] * d.tab_c1[oi];
+                hv = caxpy(hv, M5 + adt * TAB(d.tab_lv, 0, j, s), d.v[oi]);
             }
         }
         if (j >= 1 && j <= N - 2) {
-            double L5[5];
-            eta_band(d, j, m, al, L5);
             const int st = d.start[j];
             for (int s = 0; s < 5; ++s) {
+                const double ri = d.rinv[st + s];
+                const double L5 = d.nu * (d.l2[j * 5 + s] - d.d0[j * 5 + s] * (al * al + m * m * ri * ri));
                 const double2 x = d.eta[(size_t)(st + s) * P + pair];
-                he = caxpy(he, d.d0[j * 5 + s] + adt * L5[s], x);
+                he = caxpy(he, d.d0[j * 5 + s] + adt * L5, x);
             }
         }
         d.Hv[o] = hv;
@@ -921,6 +952,29 @@ void tc_launch_strain(const TcDev& d, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// After a field is set: zero the (0,0) slot and the axial Nyquist slot, and
+// make the m = 0 column Hermitian (slot Nz - n = conj(slot n)), so that the
+// field is real.  One thread per (r, element) of the j = 0 column and of the
+// Nyquist slot.
+__global__ void __launch_bounds__(256) k_realify(TcDev d, double2* f) {
+    const int r = blockIdx.y;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Nz = d.Nz, Nh = d.Nh;
+    if (r >= d.Nr || idx >= Nz + Nh) return;
+    double2* pl = f + (size_t)r * d.npairs;
+    if (idx < Nz) {
+        const int s = idx;                               // slot of the j = 0 column
+        if (s == 0) pl[0] = cz();
+        else if (s > Nz / 2) pl[(size_t)s * Nh] = cconj(pl[(size_t)(Nz - s) * Nh]);
+    } else {
+        pl[(size_t)(Nz / 2) * Nh + (idx - Nz)] = cz();   // Nyquist slot, every j
+    }
+}
+
+void tc_launch_realify(const TcDev& d, double2* field, cudaStream_t s) {
+    k_realify<<<dim3((d.Nz + d.Nh + 255) / 256, d.Nr), 256, 0, s>>>(d, field);
+}
+
 void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
     k_setup<<<(d.npairs + 127) / 128, 128, 0, s>>>(d);
 }
