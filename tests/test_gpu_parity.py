@@ -220,14 +220,18 @@ def test_laminar_state_stays_laminar():
         tc.tc_destroy(h)
 
 
-def test_nonfinite_state_is_reported():
-    """A NaN planted in the host input makes tc_step return TC_ERR_NONFINITE
-    (no device fault: the kernels only test values)."""
+@pytest.mark.parametrize("precision", [tc.TC_PREC_FP64, tc.TC_PREC_MIXED, tc.TC_PREC_DF64])
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_nonfinite_state_is_reported(precision, bad):
+    """A NaN or an infinity planted in the host input makes tc_step return
+    TC_ERR_NONFINITE in every form, through the float32 and double-float
+    conversions of the state (no device fault: the kernels only test values)."""
     v, e = workload_inputs("tc-small-33x16x16")
     v = v.copy()
-    v[10, 2, 3] = np.nan
+    v[10, 2, 3] = bad
     cfg = SMALL
-    h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"], v=v, eta=e)
+    h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"], v=v, eta=e,
+                 precision=precision)
     try:
         with pytest.raises(tc.TcError) as ex:
             tc.tc_step(h, 1)
