@@ -345,18 +345,27 @@ def run_gpu(args):
         pin["vi"].numpy().view(np.complex128)[:] = v.ravel()
         pin["ei"].numpy().view(np.complex128)[:] = e.ravel()
         torch.cuda.synchronize()
+        part = {"h2d": 0.0, "step": 0.0, "d2h": 0.0, "stats": 0.0}
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            ta = time.perf_counter()
             tc.tc_set_field_ptr(h, tc.TC_FIELD_V, pin["vi"].data_ptr(), nb)
             tc.tc_set_field_ptr(h, tc.TC_FIELD_ETA, pin["ei"].data_ptr(), nb)
+            tb = time.perf_counter()
             tc.tc_step(h, 1)
+            tcs = time.perf_counter()
             tc.tc_get_field_ptr(h, tc.TC_FIELD_V, tc.TC_SPECTRAL, pin["vo"].data_ptr(), nb)
             tc.tc_get_field_ptr(h, tc.TC_FIELD_ETA, tc.TC_SPECTRAL, pin["eo"].data_ptr(), nb)
+            td = time.perf_counter()
             stats = tc.tc_torque_stats(h)
+            te = time.perf_counter()
+            for k, dt_ in (("h2d", tb - ta), ("step", tcs - tb), ("d2h", td - tcs), ("stats", te - td)):
+                part[k] += 1e3 * dt_ / args.e2e_steps
         wall = dist.max(time.perf_counter() - t0)
         e2e = {"value": gp * args.e2e_steps * world / wall, "unit": UNIT,
                "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + ctypes.sizeof(tc.tc_stats),
-               "steps": args.e2e_steps, "torque_inner": stats["G_inner"]}
+               "steps": args.e2e_steps, "torque_inner": stats["G_inner"],
+               "ms_per_step_by_call": {k: round(x, 2) for k, x in part.items()}}
     device_bytes = tc.tc_device_bytes(h)
     tc.tc_destroy(h)
 
