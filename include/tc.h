@@ -160,6 +160,17 @@ int tc_torque_stats(tc_handle* h, tc_stats* out);
 /* Launch stream (a cudaStream_t, or NULL for the legacy default stream). */
 int tc_set_stream(tc_handle* h, void* cuda_stream);
 
+/* Override the launch shapes the autotuner would choose (for tuning studies
+ * and tests; no counterpart in the paper; the arithmetic is the same for
+ * every choice):
+ *   ztile: azimuthal columns per block of the z transforms, 1, 2, 4 or 8,
+ *          dividing Ntheta/2 (0 keeps the current value);
+ *   line_variant: line-kernel launch shape, 64, 128 or 256 threads per
+ *          block, 1003 / 1004 (128 threads, budget for 3 / 4 blocks per
+ *          SM) or 2007 (64 threads, 144 registers); 0 keeps the current.
+ * Returns TC_ERR_ARG for other values; a captured step graph is rebuilt. */
+int tc_set_tiles(tc_handle* h, int ztile, int line_variant);
+
 /* Device bytes held by the handle. */
 size_t tc_device_bytes(const tc_handle* h);
 

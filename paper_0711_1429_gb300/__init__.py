@@ -90,6 +90,8 @@ def lib():
     L.tc_torque_stats.argtypes = [vp, ctypes.POINTER(tc_stats)]
     L.tc_set_stream.restype = i
     L.tc_set_stream.argtypes = [vp, vp]
+    L.tc_set_tiles.restype = i
+    L.tc_set_tiles.argtypes = [vp, i, i]
     L.tc_device_bytes.restype = sz
     L.tc_device_bytes.argtypes = [vp]
     L.tc_destroy.restype = None
@@ -228,6 +230,13 @@ def tc_torque_stats(h):
 
 def tc_set_stream(h, stream_ptr):
     return _check(lib().tc_set_stream(h, stream_ptr))
+
+
+LINE_VARIANTS = (64, 128, 256, 1003, 1004, 2007)
+
+
+def tc_set_tiles(h, ztile=0, line_variant=0):
+    return _check(lib().tc_set_tiles(h, ztile, line_variant))
 
 
 def tc_device_bytes(h):

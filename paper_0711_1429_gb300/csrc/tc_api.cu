@@ -359,7 +359,7 @@ int autotune(tc_handle* h) {
     d.ztile = best_t;
     best = 1e30f;
     int best_b = d.line_block;
-    for (int bs : {64, 128, 256, 1003, 1004}) {
+    for (int bs : {64, 128, 256, 1003, 1004, 2007}) {
         d.line_block = bs;
         const float ms = timed([&] { tc_launch_line_phase(d, 0, h->stream); });
         if (ms < best) { best = ms; best_b = bs; }
@@ -695,6 +695,27 @@ void tc_destroy(tc_handle* h) {
 int tc_set_stream(tc_handle* h, void* s) {
     if (!h) { set_err("null handle"); return TC_ERR_ARG; }
     h->stream = (cudaStream_t)s;
+    return TC_OK;
+}
+
+int tc_set_tiles(tc_handle* h, int ztile, int line_variant) {
+    if (!h) { set_err("null handle"); return TC_ERR_ARG; }
+    TcDev& d = h->d;
+    if (ztile != 0) {
+        if ((ztile != 1 && ztile != 2 && ztile != 4 && ztile != 8) || d.Nh % ztile ||
+            2 * (size_t)ztile * d.Mz * sizeof(double2) > 200 * 1024) {
+            set_err("ztile must be 1, 2, 4 or 8, divide Ntheta/2 and fit the shared memory");
+            return TC_ERR_ARG;
+        }
+    }
+    if (line_variant != 0 && line_variant != 64 && line_variant != 128 && line_variant != 256 &&
+        line_variant != 1003 && line_variant != 1004 && line_variant != 2007) {
+        set_err("line_variant must be 64, 128, 256, 1003, 1004 or 2007");
+        return TC_ERR_ARG;
+    }
+    if (ztile) d.ztile = ztile;
+    if (line_variant) d.line_block = line_variant;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     return TC_OK;
 }
 

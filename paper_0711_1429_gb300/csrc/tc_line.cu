@@ -421,8 +421,8 @@ __device__ __forceinline__ void inner_terms(const CT& pa, const CT& uv, const CT
     be = tadd(be, timag((T)2 * nut * mt * ri2, U));
 }
 
-template <int MODE, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
+template <int MODE>
+__device__ __forceinline__ void line_body(const TcDev& d, int k) {
     constexpr bool MIXED = (MODE == 1);
     typedef typename LineTypes<MODE>::T T;
     typedef typename LineTypes<MODE>::CT CT;
@@ -631,6 +631,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) {
     }
     reconstruct_pair(d, pair, m, al, partner);
 }
+
+// Kernel variants: a register budget from launch bounds (threads per block,
+// resident blocks per SM), or an explicit register cap.
+template <int MODE, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) { line_body<MODE>(d, k); }
+template <int MODE, int NREG>
+__global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k) { line_body<MODE>(d, k); }
 
 // ---------------------------------------------------------------------------
 // Initial RK memory H_1 = (M + alpha_1 dt L) x for v and eta, and u, w.
@@ -981,21 +988,26 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
 
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
     // line_block encodes the variant: 64/128/256 threads with the register
-    // budget of one 256-thread block per SM, or 128 threads with a budget
-    // for 3 (1003) or 4 (1004) resident blocks per SM
+    // budget of one 256-thread block per SM; 128 threads with a budget for 3
+    // (1003) or 4 (1004) resident blocks per SM; 64 threads capped at 144
+    // registers (2007: 7 resident blocks, 448 threads per SM, which splits
+    // 131 k pairs into 1.9 waves instead of 1.7)
     const int v = d.line_block > 0 ? d.line_block : 128;
-    const int bs = v > 1000 ? 128 : v;
+    const int bs = v == 2007 ? 64 : (v > 1000 ? 128 : v);
     const int grid = (d.npairs + bs - 1) / bs;
-    switch (d.prec * 10 + (v == 1003 ? 1 : v == 1004 ? 2 : 0)) {
+    switch (d.prec * 10 + (v == 1003 ? 1 : v == 1004 ? 2 : v == 2007 ? 3 : 0)) {
         case 0:  k_line<0, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
         case 1:  k_line<0, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
         case 2:  k_line<0, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+        case 3:  k_line_r<0, 144><<<grid, bs, 0, s>>>(d, k); break;
         case 10: k_line<1, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
         case 11: k_line<1, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
         case 12: k_line<1, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+        case 13: k_line_r<1, 144><<<grid, bs, 0, s>>>(d, k); break;
         case 20: k_line<2, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
         case 21: k_line<2, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
-        default: k_line<2, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+        case 22: k_line<2, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
+        default: k_line_r<2, 144><<<grid, bs, 0, s>>>(d, k); break;
     }
 }
 

@@ -401,3 +401,34 @@ def test_minimum_sizes():
         _check(c, s, h, 1e-10)
     finally:
         tc.tc_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [tc.TC_PREC_FP64, tc.TC_PREC_MIXED, tc.TC_PREC_DF64])
+def test_launch_shapes_change_no_bits(precision):
+    """Every z tile and line-kernel launch shape gives the same bits: the
+    autotuner's choice changes no arithmetic."""
+    cfg = dict(Nr=33, Ntheta=32, Nz=24, zeta=0.883, Re_i=800.0, Re_o=0.0, dt=2e-3)
+    v, e = inputs(33, 32, 24, 0.883, 9, "k2", 0.05)
+
+    def run(ztile, variant):
+        h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"],
+                     v=v, eta=e, precision=precision)
+        try:
+            tc.tc_set_tiles(h, ztile, variant)
+            tc.tc_step(h, 2)
+            return gpu_state(h, 33, 24, 16)
+        finally:
+            tc.tc_destroy(h)
+
+    ref = run(8, 128)
+    for zt, lv in [(1, 0), (2, 0), (4, 0)] + [(0, x) for x in tc.LINE_VARIANTS]:
+        g = run(zt, lv)
+        for k in ref:
+            assert np.array_equal(g[k], ref[k]), (zt, lv, k)
+    h = gpu_case(33, 32, 24, 0.883, 800.0, 0.0, 2e-3, precision=precision)
+    try:
+        for bad in ((3, 0), (0, 100), (16, 0)):
+            with pytest.raises(tc.TcError):
+                tc.tc_set_tiles(h, *bad)
+    finally:
+        tc.tc_destroy(h)
