@@ -398,6 +398,67 @@ __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* bu
 #undef TC_FFT_CASE
 }
 
+// Two transforms of one plan family (theta rows: the full length M1 and the
+// half length M2) advanced stage by stage in one loop, one barrier per
+// stage for both; each keeps its own plan, twiddles and ping-pong pair.  On
+// return a_res / b_res hold the buffers with the results.
+template <typename T, int SIGN, int M, int S>
+__device__ __forceinline__ void pair_bfly(typename V2<T>::t* src, typename V2<T>::t* dst, int j,
+                                          const typename V2<T>::t* __restrict__ tw,
+                                          const double* __restrict__ twtan) {
+    constexpr int R = plan_radix_f(M, S, 0);
+    constexpr int Ns = plan_ns_f(M, S, 0);
+    constexpr int nb = M / R;
+    if constexpr (std::is_same<T, double>::value && Ns > 1)
+        stockham_bfly_tan<R, SIGN>(src, dst, j, nb, Ns, twtan + plan_tan_off(M, S));
+    else
+        stockham_bfly<R, SIGN, T>(src, dst, j, nb, Ns, tw + plan_off_f(M, S, 0));
+}
+template <typename T, int SIGN, int M1, int M2, int S>
+__device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V2<T>::t* a1,
+                                               typename V2<T>::t* b0, typename V2<T>::t* b1,
+                                               typename V2<T>::t*& a_res, typename V2<T>::t*& b_res,
+                                               const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
+                                               const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
+    constexpr int n1 = plan_nst_f(M1, 0), n2 = plan_nst_f(M2, 0);
+    if constexpr (S >= n1 && S >= n2) {
+        a_res = a0;
+        b_res = b0;
+    } else {
+        constexpr bool A = S < n1, B = S < n2;
+        constexpr int nb1 = A ? M1 / plan_radix_f(M1, S, 0) : 0;
+        constexpr int nb2 = B ? M2 / plan_radix_f(M2, S, 0) : 0;
+        for (int b = threadIdx.x; b < nb1 + nb2; b += blockDim.x) {
+            if constexpr (A) {
+                if (b < nb1) { pair_bfly<T, SIGN, M1, (A ? S : 0)>(a0, a1, b, tw1, tt1); continue; }
+            }
+            if constexpr (B) pair_bfly<T, SIGN, M2, (B ? S : 0)>(b0, b1, b - nb1, tw2, tt2);
+        }
+        __syncthreads();
+        fft_pair_stage<T, SIGN, M1, M2, S + 1>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
+                                               a_res, b_res, tw1, tt1, tw2, tt2);
+    }
+}
+// Full-length (plan p1, one column) and half-length (plan p2, one column)
+// transforms together when both lengths have compile-time plans, else one
+// after the other.
+template <typename T, int SIGN>
+__device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename V2<T>::t* b0, typename V2<T>::t* b1,
+                         typename V2<T>::t*& a_res, typename V2<T>::t*& b_res,
+                         const FftPlan& p1, const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
+                         const FftPlan& p2, const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
+#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0>(a0, a1, b0, b1, a_res, b_res, tw1, tt1, tw2, tt2); return; } break;
+    switch (p1.M) {
+        TC_PAIR_CASE(24) TC_PAIR_CASE(36) TC_PAIR_CASE(48) TC_PAIR_CASE(72) TC_PAIR_CASE(96)
+        TC_PAIR_CASE(144) TC_PAIR_CASE(192) TC_PAIR_CASE(288) TC_PAIR_CASE(384) TC_PAIR_CASE(576)
+        TC_PAIR_CASE(768) TC_PAIR_CASE(1152) TC_PAIR_CASE(1536)
+        default: break;
+    }
+#undef TC_PAIR_CASE
+    a_res = fft<T, SIGN, 0>(a0, a1, 1, p1, tw1, tt1);
+    b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
+}
+
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twz(const TcDev& d);
 template <> __device__ __forceinline__ const dcomplex* twz<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twz_x); }
 template <> __device__ __forceinline__ const double2* twz<double>(const TcDev& d) { return d.twz_d; }
@@ -464,10 +525,14 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
 // length Mt, ww - vv through the half-length real transform:
 // z_m = b_{2m} + i b_{2m+1}, Z = FFT_H(z),
 // X_k = (Z_k + conj Z_{H-k})/2 + exp(-2 pi i k/Mt) (Z_k - conj Z_{H-k})/(2i).
+// Double-float form: 5 Mt of shared memory (two full and one half column
+// per ping-pong side), the two forward full-length transforms batched as one
+// 2-column transform.  The 4 Mt arrangement above measured slower here: the
+// double-float butterflies are latency-bound and profit from the wider
+// stages more than from the fourth resident block.
 template <typename T>
-__global__ void __launch_bounds__(256) k_rows(TcDev d) {
+__device__ __forceinline__ void rows_5mt(const TcDev& d, unsigned char* smem_raw) {
     typedef typename V2<T>::t C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
     const int H = Mt / 2;
     C* fA = reinterpret_cast<C*>(smem_raw);            // 2 full columns
@@ -558,6 +623,119 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
             pb[(((size_t)4 * Nr + r) * Mz + q) * Nh + j] = x;
         }
     }
+}
+
+// Shared memory: three full columns F1..F3 and two half columns H1, H2
+// (4 Mt complex values).  The inverse pair runs in F1/F2 and H1/H2; the
+// products (uu - vv) + i uv and (ww - vv) go to the free buffers and are
+// transformed as a pair, (uw + i vw) into F3, transformed after the first
+// pair's coefficients are written.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows(TcDev d) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (std::is_same<T, dfloat>::value) {
+        rows_5mt<T>(d, smem_raw);
+        return;
+    }
+    const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
+    const int H = Mt / 2;
+    C* F1 = reinterpret_cast<C*>(smem_raw);
+    C* F2 = F1 + Mt;
+    C* F3 = F2 + Mt;
+    C* H1 = F3 + Mt;
+    C* H2 = H1 + H;
+    const int q = blockIdx.x, r = blockIdx.y;
+    const C* zb = reinterpret_cast<const C*>(d.zbuf);
+    const C* ur = zb + (((size_t)0 * Nr + r) * Mz + q) * Nh;
+    const C* vr = zb + (((size_t)1 * Nr + r) * Mz + q) * Nh;
+    const C* wr = zb + (((size_t)2 * Nr + r) * Mz + q) * Nh;
+    const C* tr = twr<T>(d);
+    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
+        C a;
+        a.x = 0; a.y = 0;
+        if (p == 0) {
+            a.x = ur[0].x; a.y = vr[0].x;
+        } else if (p < Nh) {
+            C U = ur[p], V = vr[p];
+            a.x = U.x - V.y; a.y = U.y + V.x;
+        } else if (p > Mt - Nh) {
+            const int j = Mt - p;
+            C U = ur[j], V = vr[j];
+            a.x = U.x + V.y; a.y = V.x - U.y;
+        }
+        F1[p] = a;
+    }
+    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+        C xk, xm;
+        xk.x = 0; xk.y = 0; xm.x = 0; xm.y = 0;
+        if (k < Nh) { xk = wr[k]; if (k == 0) xk.y = 0; }
+        const int kk = H - k;
+        if (k > 0 && kk < Nh) xm = wr[kk];
+        // E = xk + conj(xm), O = (xk - conj(xm)) exp(+2 pi i k/Mt)
+        C E, Dd, O, z;
+        E.x = xk.x + xm.x; E.y = xk.y - xm.y;
+        Dd.x = xk.x - xm.x; Dd.y = xk.y + xm.y;
+        const C t = tr[k];                     // exp(-2 pi i k/Mt)
+        O.x = Dd.x * t.x + Dd.y * t.y; O.y = Dd.y * t.x - Dd.x * t.y;
+        z.x = E.x - O.y; z.y = E.y + O.x;      // E + i O
+        H1[k] = z;
+    }
+    __syncthreads();
+    C *r1, *r2;
+    fft_pair<T, +1>(F1, F2, H1, H2, r1, r2, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    C* o1 = (r1 == F1) ? F2 : F1;              // free full buffer
+    C* o2 = (r2 == H1) ? H2 : H1;              // free half buffer
+    for (int m = threadIdx.x; m < H; m += blockDim.x) {
+        const C w2 = r2[m];
+        T bb[2];
+        for (int e = 0; e < 2; ++e) {
+            const int p = 2 * m + e;
+            const T u = r1[p].x, v = r1[p].y, w = e ? w2.y : w2.x;
+            const T vv = v * v;
+            C b0, b1;
+            b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
+            b1.x = u * w; b1.y = v * w;          // uw, vw
+            o1[p] = b0; F3[p] = b1;
+            bb[e] = w * w - vv;                  // ww - vv
+        }
+        C z; z.x = bb[0]; z.y = bb[1];
+        o2[m] = z;
+    }
+    __syncthreads();
+    C *s1, *s3;
+    fft_pair<T, -1>(o1, r1, o2, r2, s1, s3, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    C* pb = reinterpret_cast<C*>(d.pbuf);
+    // unpack two real transforms from one complex transform of length Mt
+    auto unpack_full = [&](const C* out, int j, int slot) {
+        const C cj = out[j];
+        const C cm = out[j == 0 ? 0 : Mt - j];
+        C x1, x2;
+        x1.x = (T)0.5 * (cj.x + cm.x); x1.y = (T)0.5 * (cj.y - cm.y);
+        x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
+        pb[(((size_t)slot * Nr + r) * Mz + q) * Nh + j] = x1;
+        pb[(((size_t)(slot + 1) * Nr + r) * Mz + q) * Nh + j] = x2;
+    };
+    for (int idx = threadIdx.x; idx < 2 * Nh; idx += blockDim.x) {
+        if (idx < Nh) {
+            unpack_full(s1, idx, 0);                // uu - vv, uv
+        } else {
+            const int j = idx - Nh;
+            const C zk = s3[j];
+            const C zm = s3[j == 0 ? 0 : H - j];
+            C ev, od, x;
+            ev.x = (T)0.5 * (zk.x + zm.x); ev.y = (T)0.5 * (zk.y - zm.y);
+            // (Z_k - conj Z_{H-k})/(2i)
+            od.x = (T)0.5 * (zk.y + zm.y); od.y = (T)-0.5 * (zk.x - zm.x);
+            const C t = tr[j];
+            x.x = ev.x + od.x * t.x - od.y * t.y;
+            x.y = ev.y + od.x * t.y + od.y * t.x;
+            pb[(((size_t)4 * Nr + r) * Mz + q) * Nh + j] = x;   // ww - vv
+        }
+    }
+    // uw + i vw: its ping-pong partner is the full buffer not holding s1
+    C* s2 = fft<T, -1, 0>(F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), d.twt_tan);
+    for (int j = threadIdx.x; j < Nh; j += blockDim.x) unpack_full(s2, j, 2);   // uw, vw
 }
 
 // ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) -----------------
@@ -654,7 +832,8 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
     typedef typename V2<T>::t C;
     const int ct = d.ztile;
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
-    const size_t smr = 5 * (size_t)d.Mt * sizeof(C);   // 2 x (2 full + 1 half) columns
+    // 3 full + 2 half columns (double-float: 2 x (2 full + 1 half))
+    const size_t smr = (std::is_same<T, dfloat>::value ? 5 : 4) * (size_t)d.Mt * sizeof(C);
     const bool odd = z_has_odd_primes(d);
     const bool tan = std::is_same<T, double>::value && d.zfam0;
     if (which == 0) {
