@@ -367,6 +367,7 @@ def run_gpu(args):
                "steps": args.e2e_steps, "torque_inner": stats["G_inner"],
                "ms_per_step_by_call": {k: round(x, 2) for k, x in part.items()}}
     device_bytes = tc.tc_device_bytes(h)
+    zt, lv, ch = tc.tc_get_tiles(h)
     tc.tc_destroy(h)
 
     # ---- the other precision forms, same input and step count; error against this run
@@ -426,7 +427,8 @@ def run_gpu(args):
                               if device_bytes > 129e6 else "state fits in L2 (not flushed)"),
                        "device_bytes": device_bytes},
             "latency_ms": {"p50": p50, "p99": p99},
-            "gpu_launches": 15 * args.steps,
+            "gpu_launches": tc.step_kernels(ch) * args.steps,
+            "launch_shapes": {"ztile": zt, "line_variant": lv, "column_groups": ch},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clk"],
             "alu_peaks_tflops": peaks, "forms": forms, "paper_workload": paper}
     if rank == 0:

@@ -167,9 +167,19 @@ int tc_set_stream(tc_handle* h, void* cuda_stream);
  *          dividing Ntheta/2 (0 keeps the current value);
  *   line_variant: line-kernel launch shape, 64, 128 or 256 threads per
  *          block, 1003 / 1004 (128 threads, budget for 3 / 4 blocks per
- *          SM) or 2007 (64 threads, 144 registers); 0 keeps the current.
+ *          SM) or 2007 (64 threads, 144 registers); 0 keeps the current;
+ *   chunks: column groups of the step graph, in which the z transforms of
+ *          one group overlap the line kernel of another: 1 (no overlap), 2,
+ *          4 or 8, used when it divides the number of z tiles (0 keeps the
+ *          current choice, initially made from the shape).
  * Returns TC_ERR_ARG for other values; a captured step graph is rebuilt. */
-int tc_set_tiles(tc_handle* h, int ztile, int line_variant);
+int tc_set_tiles(tc_handle* h, int ztile, int line_variant, int chunks);
+
+/* The launch shapes in use (after the autotuner): z tile, line-kernel
+ * variant and column groups of the step graph (1: no overlap).  Any pointer
+ * may be NULL.  A step graph launches 15 kernels without groups and
+ * 7 + 8 * chunks with them. */
+int tc_get_tiles(const tc_handle* h, int* ztile, int* line_variant, int* chunks);
 
 /* Device bytes held by the handle. */
 size_t tc_device_bytes(const tc_handle* h);

@@ -91,7 +91,9 @@ def lib():
     L.tc_set_stream.restype = i
     L.tc_set_stream.argtypes = [vp, vp]
     L.tc_set_tiles.restype = i
-    L.tc_set_tiles.argtypes = [vp, i, i]
+    L.tc_set_tiles.argtypes = [vp, i, i, i]
+    L.tc_get_tiles.restype = i
+    L.tc_get_tiles.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.tc_device_bytes.restype = sz
     L.tc_device_bytes.argtypes = [vp]
     L.tc_destroy.restype = None
@@ -235,8 +237,20 @@ def tc_set_stream(h, stream_ptr):
 LINE_VARIANTS = (64, 128, 256, 1003, 1004, 2007)
 
 
-def tc_set_tiles(h, ztile=0, line_variant=0):
-    return _check(lib().tc_set_tiles(h, ztile, line_variant))
+def tc_set_tiles(h, ztile=0, line_variant=0, chunks=0):
+    return _check(lib().tc_set_tiles(h, ztile, line_variant, chunks))
+
+
+def tc_get_tiles(h):
+    """(ztile, line_variant, chunks) in use."""
+    z, l, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().tc_get_tiles(h, ctypes.byref(z), ctypes.byref(l), ctypes.byref(c)))
+    return z.value, l.value, c.value
+
+
+def step_kernels(chunks):
+    """Kernels one step graph launches."""
+    return 15 if chunks <= 1 else 7 + 8 * chunks
 
 
 def tc_device_bytes(h):

@@ -315,6 +315,7 @@ int upload(tc_handle* h, const T*& dst, const std::vector<T>& src) {
 void free_all(tc_handle* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
+    tcx::release_pipeline(h);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
 }
@@ -325,6 +326,7 @@ void free_all(tc_handle* h) {
 // Nz, precision).  The choice changes no arithmetic.
 std::mutex g_tune_mu;
 std::map<std::array<int, 4>, std::pair<int, int>> g_tune;
+std::map<std::array<int, 4>, int> g_tune_chunks;   // column groups chosen by tc_step
 
 int autotune(tc_handle* h) {
     TcDev& d = h->d;
@@ -593,16 +595,94 @@ int ensure_init(tc_handle* h) {
     return TC_OK;
 }
 
+int prepare_pipeline(tc_handle* h) {
+    if (h->pipe_ready) return TC_OK;
+    for (auto& st : h->aux) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (int c = 0; c < TC_MAX_CHUNKS; ++c) {
+        CK(cudaEventCreateWithFlags(&h->evz[c], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->evl[c], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&h->evm, cudaEventDisableTiming));
+    for (auto& e : h->evj) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->pipe_ready = true;
+    return TC_OK;
+}
+
+void release_pipeline(tc_handle* h) {
+    if (!h->pipe_ready) return;
+    for (auto& st : h->aux) { cudaStreamDestroy(st); st = nullptr; }
+    for (int c = 0; c < TC_MAX_CHUNKS; ++c) { cudaEventDestroy(h->evz[c]); cudaEventDestroy(h->evl[c]); }
+    cudaEventDestroy(h->evm);
+    for (auto& e : h->evj) cudaEventDestroy(e);
+    h->pipe_ready = false;
+}
+
+bool chunks_valid(const tc_handle* h, int c) {
+    const TcDev& d = h->d;
+    return c >= 1 && c <= TC_MAX_CHUNKS && (d.Nh / d.ztile) % c == 0;
+}
+
+// Column groups of the overlapped step: the value set by tc_set_tiles, else
+// the one chosen by timing (tc_step with the autotuner on), else none.
+int pipeline_chunks(const tc_handle* h) {
+    const int c = h->chunks > 0 ? h->chunks : h->chunks_auto;
+    return chunks_valid(h, c) ? c : 1;
+}
+
+// One step.  Without column groups: the 15 kernels in order.  With C groups
+// the plane and line phases overlap: the z-forward transform of group c is
+// followed at once by the line kernel of group c (its pairs need only that
+// group's products), whose output feeds the next substep's z-inverse
+// transform of group c; the mean flow needs the j = 0 column (group 0) and
+// must precede the z inverse of group 0 (its (0,0) slot holds U, W).  The
+// theta rows of each substep wait for every group.  The line kernels of
+// alternate groups use two streams so that they overlap too.
 void launch_step(tc_handle* h, cudaStream_t s) {
+    TcDev& d = h->d;
+    const int C = h->pipe_ready ? pipeline_chunks(h) : 1;
+    if (C <= 1) {
+        for (int k = 0; k < 3; ++k) {
+            tc_launch_plane_phase(d, s);
+            tc_launch_line_phase(d, k, s);
+            tc_launch_mean_phase(d, k, s);
+        }
+        return;
+    }
+    const int tpc = (d.Nh / d.ztile) / C;      // z tiles per group
+    const int cw = tpc * d.ztile;              // columns per group
+    cudaStream_t sM = h->aux[2], sZ = h->aux[3];
+    tc_launch_plane_kernel(d, 0, s);           // z inverse of the first substep
     for (int k = 0; k < 3; ++k) {
-        tc_launch_plane_phase(h->d, s);
-        tc_launch_line_phase(h->d, k, s);
-        tc_launch_mean_phase(h->d, k, s);
+        tc_launch_plane_kernel(d, 1, s);       // theta rows and products
+        for (int c = 0; c < C; ++c) {
+            tc_launch_plane_kernel_tiles(d, 2, s, c * tpc, tpc);
+            cudaEventRecord(h->evz[c], s);
+        }
+        cudaStreamWaitEvent(sM, h->evz[0], 0);
+        tc_launch_mean_phase(d, k, sM);
+        cudaEventRecord(h->evm, sM);
+        for (int c = 0; c < C; ++c) {
+            cudaStream_t sL = h->aux[c & 1];
+            cudaStreamWaitEvent(sL, h->evz[c], 0);
+            tc_launch_line_chunk(d, k, sL, c * cw, cw);
+            cudaEventRecord(h->evl[c], sL);
+            if (k < 2) {
+                cudaStreamWaitEvent(sZ, h->evl[c], 0);
+                if (c == 0) cudaStreamWaitEvent(sZ, h->evm, 0);
+                tc_launch_plane_kernel_tiles(d, 0, sZ, c * tpc, tpc);
+            }
+        }
+        for (int a = 0; a < (k < 2 ? 4 : 3); ++a) {
+            cudaEventRecord(h->evj[a], h->aux[a]);
+            cudaStreamWaitEvent(s, h->evj[a], 0);
+        }
     }
 }
 
 int ensure_graph(tc_handle* h) {
     if (h->graph) return TC_OK;
+    int rc_;
+    if ((rc_ = prepare_pipeline(h))) return rc_;
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g;
@@ -698,7 +778,15 @@ int tc_set_stream(tc_handle* h, void* s) {
     return TC_OK;
 }
 
-int tc_set_tiles(tc_handle* h, int ztile, int line_variant) {
+int tc_get_tiles(const tc_handle* h, int* ztile, int* line_variant, int* chunks) {
+    if (!h) { set_err("null handle"); return TC_ERR_ARG; }
+    if (ztile) *ztile = h->d.ztile;
+    if (line_variant) *line_variant = h->d.line_block > 0 ? h->d.line_block : 128;
+    if (chunks) *chunks = tcx::pipeline_chunks(h);
+    return TC_OK;
+}
+
+int tc_set_tiles(tc_handle* h, int ztile, int line_variant, int chunks) {
     if (!h) { set_err("null handle"); return TC_ERR_ARG; }
     TcDev& d = h->d;
     if (ztile != 0) {
@@ -713,8 +801,13 @@ int tc_set_tiles(tc_handle* h, int ztile, int line_variant) {
         set_err("line_variant must be 64, 128, 256, 1003, 1004 or 2007");
         return TC_ERR_ARG;
     }
+    if (chunks != 0 && chunks != 1 && chunks != 2 && chunks != 4 && chunks != 8) {
+        set_err("chunks must be 1, 2, 4 or 8");
+        return TC_ERR_ARG;
+    }
     if (ztile) d.ztile = ztile;
     if (line_variant) d.line_block = line_variant;
+    if (chunks) h->chunks = chunks;
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     return TC_OK;
 }
@@ -728,6 +821,58 @@ int tcx::check_flags(tc_handle* h) {
     return TC_OK;
 }
 using tcx::check_flags;
+
+namespace {
+// With the autotuner on and no grouping set, the first tc_step of three or
+// more steps runs one step with each candidate grouping (1 and 2 column
+// groups), timed with events, and keeps the faster for this handle and the
+// shape class.  Every grouping gives the same bits, so the tuning steps are
+// ordinary steps.
+int tune_chunks(tc_handle* h, int nsteps, int* done) {
+    *done = 0;
+    if (!h->prm.autotune || h->chunks > 0 || h->chunks_auto > 0) return TC_OK;
+    TcDev& d = h->d;
+    const std::array<int, 4> key = {d.Nr, 2 * d.Nh, d.Nz, d.prec};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_chunks.find(key);
+        if (it != g_tune_chunks.end()) {
+            h->chunks_auto = it->second;
+            if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+            return TC_OK;
+        }
+    }
+    if (!tcx::chunks_valid(h, 2)) { h->chunks_auto = 1; return TC_OK; }
+    if (nsteps < 3) return TC_OK;              // decide on a later, longer call
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    int bestc = 1;
+    for (int c : {1, 2}) {
+        h->chunks_auto = c;
+        if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+        int rc = ensure_graph(h);
+        if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
+        CK(cudaGraphUpload(h->graph, h->stream));
+        CK(cudaEventRecord(a, h->stream));
+        CK(cudaGraphLaunch(h->graph, h->stream));
+        CK(cudaEventRecord(b, h->stream));
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) { best = ms; bestc = c; }
+        ++*done;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->chunks_auto = bestc;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_chunks[key] = bestc;
+    return TC_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -753,8 +898,10 @@ int tc_step(tc_handle* h, int nsteps) {
     if (h->phase != 0) { set_err("tc_step called inside a step; finish it with tc_advance_substeps"); return TC_ERR_ARG; }
     int rc;
     if ((rc = ensure_init(h))) return rc;
+    int done = 0;
+    if ((rc = tune_chunks(h, nsteps, &done))) return rc;
     if ((rc = ensure_graph(h))) return rc;
-    for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->graph, h->stream));
+    for (int n = done; n < nsteps; ++n) CK(cudaGraphLaunch(h->graph, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->t += nsteps * h->d.dt;
     h->step += nsteps;

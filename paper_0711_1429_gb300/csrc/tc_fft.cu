@@ -484,13 +484,13 @@ template <> __device__ __forceinline__ const float2* twr<float>(const TcDev& d) 
 template <typename T, int ZF>
 __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict__ f0,
                                               const double2* __restrict__ f1,
-                                              const double2* __restrict__ f2) {
+                                              const double2* __restrict__ f2, int tile0) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     const int ct = d.ztile;
     C* buf1 = buf0 + ct * d.Mz;
-    const int j0 = blockIdx.x * ct;
+    const int j0 = (blockIdx.x + tile0) * ct;
     const int r = blockIdx.y;
     const int f = blockIdx.z;
     const double2* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
@@ -740,13 +740,13 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
 
 // ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) -----------------
 template <typename T, int ZF>
-__global__ void __launch_bounds__(256) k_zfwd(TcDev d) {
+__global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     const int ct = d.ztile;
     C* buf1 = buf0 + ct * d.Mz;
-    const int j0 = blockIdx.x * ct;
+    const int j0 = (blockIdx.x + tile0) * ct;
     const int r = blockIdx.y;
     const int p = blockIdx.z;
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh, Nr = d.Nr;
@@ -828,7 +828,7 @@ static bool z_has_odd_primes(const TcDev& d) {
 }
 
 template <typename T>
-static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
+static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles) {
     typedef typename V2<T>::t C;
     const int ct = d.ztile;
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
@@ -837,22 +837,28 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s) {
     const bool odd = z_has_odd_primes(d);
     const bool tan = std::is_same<T, double>::value && d.zfam0;
     if (which == 0) {
-        if (odd) k_zinv<T, 2><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
-        else if (tan) k_zinv<double, 0><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
-        else k_zinv<T, 1><<<dim3(d.Nh / ct, d.Nr, 3), 256, smz, s>>>(d, d.u, d.v, d.w);
+        const dim3 g(ntiles, d.Nr, 3);
+        if (odd) k_zinv<T, 2><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
+        else if (tan) k_zinv<double, 0><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
+        else k_zinv<T, 1><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
     } else if (which == 1) {
         k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
     } else {
-        if (odd) k_zfwd<T, 2><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
-        else if (tan) k_zfwd<double, 0><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
-        else k_zfwd<T, 1><<<dim3(d.Nh / ct, d.Nr, TC_NPROD), 256, smz, s>>>(d);
+        const dim3 g(ntiles, d.Nr, TC_NPROD);
+        if (odd) k_zfwd<T, 2><<<g, 256, smz, s>>>(d, tile0);
+        else if (tan) k_zfwd<double, 0><<<g, 256, smz, s>>>(d, tile0);
+        else k_zfwd<T, 1><<<g, 256, smz, s>>>(d, tile0);
     }
 }
 
+void tc_launch_plane_kernel_tiles(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles) {
+    if (d.prec == 1) plane_kernel_t<float>(d, which, s, tile0, ntiles);
+    else if (d.prec == 2) plane_kernel_t<dfloat>(d, which, s, tile0, ntiles);
+    else plane_kernel_t<double>(d, which, s, tile0, ntiles);
+}
+
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s) {
-    if (d.prec == 1) plane_kernel_t<float>(d, which, s);
-    else if (d.prec == 2) plane_kernel_t<dfloat>(d, which, s);
-    else plane_kernel_t<double>(d, which, s);
+    tc_launch_plane_kernel_tiles(d, which, s, 0, d.Nh / d.ztile);
 }
 
 void tc_launch_plane_phase(const TcDev& d, cudaStream_t s) {
@@ -864,9 +870,9 @@ void tc_launch_to_physical(const TcDev& d, const double2* field, cudaStream_t s)
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(double2);
     TcDev dd = d;
     // one field through slot 0 of zbuf (always float64 here)
-    if (z_has_odd_primes(d)) k_zinv<double, 2><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
-    else if (d.zfam0) k_zinv<double, 0><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
-    else k_zinv<double, 1><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field);
+    if (z_has_odd_primes(d)) k_zinv<double, 2><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field, 0);
+    else if (d.zfam0) k_zinv<double, 0><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field, 0);
+    else k_zinv<double, 1><<<dim3(d.Nh / ct, d.Nr, 1), 256, smz, s>>>(dd, field, field, field, 0);
     k_rows_phys<<<dim3(d.Mz, d.Nr), 256, 2 * (size_t)d.Mt * sizeof(double2), s>>>(dd);
 }
 

@@ -12,6 +12,8 @@ struct HostStencils {
     std::vector<double> d0, l1, l2, l4, dwall, dsol;
 };
 
+#define TC_MAX_CHUNKS 8
+
 struct tc_handle {
     tc_params prm;
     TcDev d;
@@ -28,6 +30,15 @@ struct tc_handle {
     HostStencils S;
     double Ri = 0, Ro = 0;
     cudaStream_t own_stream = nullptr;   // created by the batch / server
+    // overlap of the plane and line phases inside a captured step: the
+    // azimuthal columns are split into `chunks` groups of z tiles; aux
+    // streams 0, 1 run the line kernel of alternate chunks, 2 the mean flow,
+    // 3 the next substep's z inverse (0 chunks: chosen from the shape)
+    int chunks = 0;                // set by tc_set_tiles (0: automatic)
+    int chunks_auto = 0;           // chosen by timing the first steps (0: not yet)
+    bool pipe_ready = false;
+    cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t evz[TC_MAX_CHUNKS] = {}, evl[TC_MAX_CHUNKS] = {}, evm = nullptr, evj[4] = {};
 };
 
 namespace tcx {
@@ -35,6 +46,10 @@ void set_err(const std::string& s);
 int ensure_init(tc_handle* h);                 // H_1 and u, w of the current state
 void launch_step(tc_handle* h, cudaStream_t s);  // the 15 kernels of one step
 int ensure_graph(tc_handle* h);
+int prepare_pipeline(tc_handle* h);           // aux streams and events (before any capture)
+int pipeline_chunks(const tc_handle* h);      // column groups of the overlapped step (1: none)
+bool chunks_valid(const tc_handle* h, int c);
+void release_pipeline(tc_handle* h);
 int check_flags(tc_handle* h);
 size_t estimate_device_bytes(const tc_params& p);
 int validate(const tc_params* p);

@@ -119,8 +119,12 @@ struct TcDev {
 void tc_launch_plane_phase(const TcDev& d, cudaStream_t s);
 // one kernel of the plane phase: 0 = z inverse, 1 = theta rows + products, 2 = z forward
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s);
+// z kernels (which = 0 or 2) on the z tiles tile0 .. tile0 + ntiles - 1 only
+void tc_launch_plane_kernel_tiles(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles);
 cudaError_t tc_probe_fma(double* fp64_tflops, double* fp32_tflops);
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s);
+// line phase of the pairs with azimuthal index j0 <= j < j0 + nj (all axial slots)
+void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int j0, int nj);
 void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s);
 void tc_launch_setup_tables(const TcDev& d, cudaStream_t s);
 void tc_launch_init_state(const TcDev& d, cudaStream_t s);

@@ -422,12 +422,14 @@ __device__ __forceinline__ void inner_terms(const CT& pa, const CT& uv, const CT
 }
 
 template <int MODE>
-__device__ __forceinline__ void line_body(const TcDev& d, int k) {
+__device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw) {
     constexpr bool MIXED = (MODE == 1);
     typedef typename LineTypes<MODE>::T T;
     typedef typename LineTypes<MODE>::CT CT;
-    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pair >= d.npairs) return;
+    // thread -> pair among the columns ja .. ja + jw - 1 of every axial slot
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= d.Nz * jw) return;
+    const int pair = (idx / jw) * d.Nh + ja + idx % jw;
     double m, al;
     long long partner;
     if (!pair_info(d, pair, m, al, partner)) return;
@@ -635,9 +637,9 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k) {
 // Kernel variants: a register budget from launch bounds (threads per block,
 // resident blocks per SM), or an explicit register cap.
 template <int MODE, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k) { line_body<MODE>(d, k); }
+__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k, int ja, int jw) { line_body<MODE>(d, k, ja, jw); }
 template <int MODE, int NREG>
-__global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k) { line_body<MODE>(d, k); }
+__global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k, int ja, int jw) { line_body<MODE>(d, k, ja, jw); }
 
 // ---------------------------------------------------------------------------
 // Initial RK memory H_1 = (M + alpha_1 dt L) x for v and eta, and u, w.
@@ -986,7 +988,9 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
     k_setup<<<(d.npairs + 127) / 128, 128, 0, s>>>(d);
 }
 
-void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
+void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) { tc_launch_line_chunk(d, k, s, 0, d.Nh); }
+
+void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int ja, int jw) {
     // line_block encodes the variant: 64/128/256 threads with the register
     // budget of one 256-thread block per SM; 128 threads with a budget for 3
     // (1003) or 4 (1004) resident blocks per SM; 64 threads capped at 144
@@ -994,20 +998,20 @@ void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) {
     // 131 k pairs into 1.9 waves instead of 1.7)
     const int v = d.line_block > 0 ? d.line_block : 128;
     const int bs = v == 2007 ? 64 : (v > 1000 ? 128 : v);
-    const int grid = (d.npairs + bs - 1) / bs;
+    const int grid = (d.Nz * jw + bs - 1) / bs;
     switch (d.prec * 10 + (v == 1003 ? 1 : v == 1004 ? 2 : v == 2007 ? 3 : 0)) {
-        case 0:  k_line<0, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
-        case 1:  k_line<0, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
-        case 2:  k_line<0, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
-        case 3:  k_line_r<0, 144><<<grid, bs, 0, s>>>(d, k); break;
-        case 10: k_line<1, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
-        case 11: k_line<1, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
-        case 12: k_line<1, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
-        case 13: k_line_r<1, 144><<<grid, bs, 0, s>>>(d, k); break;
-        case 20: k_line<2, 256, 1><<<grid, bs, 0, s>>>(d, k); break;
-        case 21: k_line<2, 128, 3><<<grid, bs, 0, s>>>(d, k); break;
-        case 22: k_line<2, 128, 4><<<grid, bs, 0, s>>>(d, k); break;
-        default: k_line_r<2, 144><<<grid, bs, 0, s>>>(d, k); break;
+        case 0:  k_line<0, 256, 1><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 1:  k_line<0, 128, 3><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 2:  k_line<0, 128, 4><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 3:  k_line_r<0, 144><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 10: k_line<1, 256, 1><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 11: k_line<1, 128, 3><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 12: k_line<1, 128, 4><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 13: k_line_r<1, 144><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 20: k_line<2, 256, 1><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 21: k_line<2, 128, 3><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        case 22: k_line<2, 128, 4><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
+        default: k_line_r<2, 144><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
     }
 }
 

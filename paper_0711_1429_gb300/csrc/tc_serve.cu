@@ -59,6 +59,7 @@ static int batch_graph(tc_batch* b) {
     const int n = (int)b->cases.size();
     for (int i = 0; i < n; ++i) {
         int rc = tcx::ensure_init(b->cases[i]);
+        if (!rc) rc = tcx::prepare_pipeline(b->cases[i]);
         if (rc) return rc;
     }
     CKR(cudaStreamSynchronize(nullptr), TC_ERR_CUDA);

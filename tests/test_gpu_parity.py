@@ -405,29 +405,32 @@ def test_minimum_sizes():
 
 @pytest.mark.parametrize("precision", [tc.TC_PREC_FP64, tc.TC_PREC_MIXED, tc.TC_PREC_DF64])
 def test_launch_shapes_change_no_bits(precision):
-    """Every z tile and line-kernel launch shape gives the same bits: the
-    autotuner's choice changes no arithmetic."""
+    """Every z tile, line-kernel launch shape and column grouping of the
+    overlapped step gives the same bits: the autotuner's choice and the
+    overlap change no arithmetic (the overlapped step's dependencies are
+    complete, or a group would read stale data)."""
     cfg = dict(Nr=33, Ntheta=32, Nz=24, zeta=0.883, Re_i=800.0, Re_o=0.0, dt=2e-3)
     v, e = inputs(33, 32, 24, 0.883, 9, "k2", 0.05)
 
-    def run(ztile, variant):
+    def run(ztile, variant, chunks):
         h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"],
                      v=v, eta=e, precision=precision)
         try:
-            tc.tc_set_tiles(h, ztile, variant)
+            tc.tc_set_tiles(h, ztile, variant, chunks)
             tc.tc_step(h, 2)
             return gpu_state(h, 33, 24, 16)
         finally:
             tc.tc_destroy(h)
 
-    ref = run(8, 128)
-    for zt, lv in [(1, 0), (2, 0), (4, 0)] + [(0, x) for x in tc.LINE_VARIANTS]:
-        g = run(zt, lv)
+    ref = run(8, 128, 1)
+    for zt, lv, ch in [(1, 0, 0), (2, 0, 0), (4, 0, 0)] + [(0, x, 0) for x in tc.LINE_VARIANTS] + \
+            [(1, 0, 2), (1, 0, 4), (1, 0, 8), (2, 0, 8)]:
+        g = run(zt, lv, ch)
         for k in ref:
-            assert np.array_equal(g[k], ref[k]), (zt, lv, k)
+            assert np.array_equal(g[k], ref[k]), (zt, lv, ch, k)
     h = gpu_case(33, 32, 24, 0.883, 800.0, 0.0, 2e-3, precision=precision)
     try:
-        for bad in ((3, 0), (0, 100), (16, 0)):
+        for bad in ((3, 0, 0), (0, 100, 0), (16, 0, 0), (0, 0, 3)):
             with pytest.raises(tc.TcError):
                 tc.tc_set_tiles(h, *bad)
     finally:
