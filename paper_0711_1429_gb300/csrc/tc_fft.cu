@@ -17,10 +17,13 @@
 //             gradient, which the pressure-free v and eta rows annihilate.
 //   k_zfwd  : per (product, r, tile): forward complex FFT in z, truncation to
 //             the Nz slots and scaling by 1/(Mt Mz).
-// All transforms are mixed-radix Stockham FFTs in shared memory: radix 3,
-// 16, then 8, 4 or 2, then the odd primes 5..17 of the axial length.
-// Template parameter T is the arithmetic type (double, or float in the
-// mixed-precision form).
+// All transforms are mixed-radix Stockham FFTs in shared memory.  Float64:
+// radix 3, then 4, then 2, with the stage twiddles in tangent form (fewer
+// float64 instructions); float32 and double-float z columns: radix 3, 16,
+// then 8, 4 or 2; axial lengths with odd prime factors add paired prime
+// stages (5..17).
+// Template parameter T is the arithmetic type: double, float (mixed form) or
+// dfloat (double-float form).
 #include "tc_internal.h"
 #include "tc_dfloat.h"
 #include <type_traits>

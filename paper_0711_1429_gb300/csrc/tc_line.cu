@@ -366,7 +366,9 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 }
 
 // ---------------------------------------------------------------------------
-// One substep of the line phase for every pair.
+// One substep of the line phase, one thread per Fourier pair, for the pairs
+// of the azimuthal columns ja .. ja + jw - 1 in every axial slot (all pairs
+// when ja = 0, jw = Ntheta/2).
 //
 // Explicit rows E (Eq. 6 rows 2..Nr-3, Eq. 7 rows 1..Nr-2) are sums over the
 // 5 stencil points of d0 . A + l1 . B (+ l2 . C for v), where A, B, C are
@@ -382,10 +384,12 @@ __device__ void reconstruct_pair(const TcDev& d, int pair, double m, double al, 
 //        B = -i m uv/r + i alpha vw + 2 i nu m u/r^2
 // (the terms of Eqs. 6-7 regrouped per stencil; the vv parts cancel because
 // c k^2 = 1).  In the mixed form everything except the continuity term is
-// formed in float32 from the float32 products; in the double-float form all
-// explicit rows are formed in double-float arithmetic (float32 pipe) from the
-// double-float products; the right sides, the solves, the RK memory and the
+// formed in float32 from the float32 products, and the continuity term in
+// double-float arithmetic; in the double-float form all explicit rows are
+// formed in double-float arithmetic (float32 pipe) from the double-float
+// products; the right sides, the solves, the RK memory and the
 // reconstruction are float64 in every form.
+//
 // Inner functions of the explicit rows at one radial point, from the five
 // products and u, v, w: A, B, C of the v rows (C without the continuity
 // term) and A, B of the eta rows, as listed above.
