@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=2.0, help="served: arrival window (s)")
     p.add_argument("--serve-rate", type=float, default=20.0, help="served: Poisson rate (1/s)")
     p.add_argument("--budget-gb", type=float, default=150.0, help="served: device budget")
+    p.add_argument("--column-groups", type=int, default=0,
+                   help="pin the column groups of the step graph (0: chosen by timing)")
     return p.parse_args()
 
 
@@ -256,6 +258,8 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False)
     tc.tc_set_stream(h, stream.cuda_stream)
     tc.tc_set_field(h, tc.TC_FIELD_V, v)
     tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
+    if args.column_groups:
+        tc.tc_set_tiles(h, 0, 0, args.column_groups)
     tc.tc_step(h, max(args.warmup, 3))
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if measure_clocks else None

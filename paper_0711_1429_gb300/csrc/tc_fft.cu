@@ -420,7 +420,7 @@ __device__ __forceinline__ void pair_bfly(typename V2<T>::t* src, typename V2<T>
 template <typename T, int SIGN, int M1, int M2, int S>
 __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V2<T>::t* a1,
                                                typename V2<T>::t* b0, typename V2<T>::t* b1,
-                                               typename V2<T>::t*& a_res, typename V2<T>::t*& b_res,
+                                               typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                                                const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
                                                const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
     constexpr int n1 = plan_nst_f(M1, 0), n2 = plan_nst_f(M2, 0);
@@ -431,34 +431,41 @@ __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V
         constexpr bool A = S < n1, B = S < n2;
         constexpr int nb1 = A ? M1 / plan_radix_f(M1, S, 0) : 0;
         constexpr int nb2 = B ? M2 / plan_radix_f(M2, S, 0) : 0;
-        for (int b = threadIdx.x; b < nb1 + nb2; b += blockDim.x) {
+        const int nA = A ? na * nb1 : 0;
+        for (int b = threadIdx.x; b < nA + nb2; b += blockDim.x) {
             if constexpr (A) {
-                if (b < nb1) { pair_bfly<T, SIGN, M1, (A ? S : 0)>(a0, a1, b, tw1, tt1); continue; }
+                if (b < nA) {
+                    const int col = b / nb1;
+                    pair_bfly<T, SIGN, M1, (A ? S : 0)>(a0 + col * M1, a1 + col * M1, b - col * nb1, tw1, tt1);
+                    continue;
+                }
             }
-            if constexpr (B) pair_bfly<T, SIGN, M2, (B ? S : 0)>(b0, b1, b - nb1, tw2, tt2);
+            if constexpr (B) pair_bfly<T, SIGN, M2, (B ? S : 0)>(b0, b1, b - nA, tw2, tt2);
         }
         __syncthreads();
         fft_pair_stage<T, SIGN, M1, M2, S + 1>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
-                                               a_res, b_res, tw1, tt1, tw2, tt2);
+                                               a_res, b_res, na, tw1, tt1, tw2, tt2);
     }
 }
-// Full-length (plan p1, one column) and half-length (plan p2, one column)
-// transforms together when both lengths have compile-time plans, else one
-// after the other.
-template <typename T, int SIGN>
+// Full-length (plan p1, na contiguous columns) and half-length (plan p2,
+// one column) transforms together when FUSE is set and both lengths have
+// compile-time plans, else one after the other.
+template <typename T, int SIGN, bool FUSE>
 __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename V2<T>::t* b0, typename V2<T>::t* b1,
-                         typename V2<T>::t*& a_res, typename V2<T>::t*& b_res,
+                         typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                          const FftPlan& p1, const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
                          const FftPlan& p2, const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
-#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0>(a0, a1, b0, b1, a_res, b_res, tw1, tt1, tw2, tt2); return; } break;
-    switch (p1.M) {
-        TC_PAIR_CASE(24) TC_PAIR_CASE(36) TC_PAIR_CASE(48) TC_PAIR_CASE(72) TC_PAIR_CASE(96)
-        TC_PAIR_CASE(144) TC_PAIR_CASE(192) TC_PAIR_CASE(288) TC_PAIR_CASE(384) TC_PAIR_CASE(576)
-        TC_PAIR_CASE(768) TC_PAIR_CASE(1152) TC_PAIR_CASE(1536)
-        default: break;
+#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0>(a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
+    if constexpr (FUSE) {
+        switch (p1.M) {
+            TC_PAIR_CASE(24) TC_PAIR_CASE(36) TC_PAIR_CASE(48) TC_PAIR_CASE(72) TC_PAIR_CASE(96)
+            TC_PAIR_CASE(144) TC_PAIR_CASE(192) TC_PAIR_CASE(288) TC_PAIR_CASE(384) TC_PAIR_CASE(576)
+            TC_PAIR_CASE(768) TC_PAIR_CASE(1152) TC_PAIR_CASE(1536)
+            default: break;
+        }
     }
 #undef TC_PAIR_CASE
-    a_res = fft<T, SIGN, 0>(a0, a1, 1, p1, tw1, tt1);
+    a_res = fft<T, SIGN, 0>(a0, a1, na, p1, tw1, tt1);
     b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
 }
 
@@ -528,126 +535,38 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
 // length Mt, ww - vv through the half-length real transform:
 // z_m = b_{2m} + i b_{2m+1}, Z = FFT_H(z),
 // X_k = (Z_k + conj Z_{H-k})/2 + exp(-2 pi i k/Mt) (Z_k - conj Z_{H-k})/(2i).
-// Double-float form: 5 Mt of shared memory (two full and one half column
-// per ping-pong side), the two forward full-length transforms batched as one
-// 2-column transform.  The 4 Mt arrangement above measured slower here: the
-// double-float butterflies are latency-bound and profit from the wider
-// stages more than from the fourth resident block.
-template <typename T>
-__device__ __forceinline__ void rows_5mt(const TcDev& d, unsigned char* smem_raw) {
-    typedef typename V2<T>::t C;
-    const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
-    const int H = Mt / 2;
-    C* fA = reinterpret_cast<C*>(smem_raw);            // 2 full columns
-    C* hA = fA + 2 * Mt;                                // 1 half column
-    C* fB = hA + H;
-    C* hB = fB + 2 * Mt;
-    const int q = blockIdx.x, r = blockIdx.y;
-    const C* zb = reinterpret_cast<const C*>(d.zbuf);
-    const C* ur = zb + (((size_t)0 * Nr + r) * Mz + q) * Nh;
-    const C* vr = zb + (((size_t)1 * Nr + r) * Mz + q) * Nh;
-    const C* wr = zb + (((size_t)2 * Nr + r) * Mz + q) * Nh;
-    const C* tr = twr<T>(d);
-    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
-        C a;
-        a.x = 0; a.y = 0;
-        if (p == 0) {
-            a.x = ur[0].x; a.y = vr[0].x;
-        } else if (p < Nh) {
-            C U = ur[p], V = vr[p];
-            a.x = U.x - V.y; a.y = U.y + V.x;
-        } else if (p > Mt - Nh) {
-            const int j = Mt - p;
-            C U = ur[j], V = vr[j];
-            a.x = U.x + V.y; a.y = V.x - U.y;
-        }
-        fA[p] = a;
-    }
-    for (int k = threadIdx.x; k < H; k += blockDim.x) {
-        C xk, xm;
-        xk.x = 0; xk.y = 0; xm.x = 0; xm.y = 0;
-        if (k < Nh) { xk = wr[k]; if (k == 0) xk.y = 0; }
-        const int kk = H - k;
-        if (k > 0 && kk < Nh) xm = wr[kk];
-        // E = xk + conj(xm), O = (xk - conj(xm)) exp(+2 pi i k/Mt)
-        C E, Dd, O, z;
-        E.x = xk.x + xm.x; E.y = xk.y - xm.y;
-        Dd.x = xk.x - xm.x; Dd.y = xk.y + xm.y;
-        const C t = tr[k];                     // exp(-2 pi i k/Mt)
-        O.x = Dd.x * t.x + Dd.y * t.y; O.y = Dd.y * t.x - Dd.x * t.y;
-        z.x = E.x - O.y; z.y = E.y + O.x;      // E + i O
-        hA[k] = z;
-    }
-    __syncthreads();
-    C* r1 = fft<T, +1, 0>(fA, fB, 1, d.pt, twt<T>(d), d.twt_tan);
-    C* r2 = fft<T, +1, 0>(hA, hB, 1, d.ph, twh<T>(d), d.twh_tan);
-    C* o1 = (r1 == fA) ? fB : fA;
-    C* o2 = (r2 == hA) ? hB : hA;
-    for (int m = threadIdx.x; m < H; m += blockDim.x) {
-        const C w2 = r2[m];
-        T bb[2];
-        for (int e = 0; e < 2; ++e) {
-            const int p = 2 * m + e;
-            const T u = r1[p].x, v = r1[p].y, w = e ? w2.y : w2.x;
-            const T vv = v * v;
-            C b0, b1;
-            b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
-            b1.x = u * w; b1.y = v * w;          // uw, vw
-            o1[p] = b0; o1[Mt + p] = b1;
-            bb[e] = w * w - vv;                  // ww - vv
-        }
-        C z; z.x = bb[0]; z.y = bb[1];
-        o2[m] = z;
-    }
-    __syncthreads();
-    C* out = fft<T, -1, 0>(o1, r1, 2, d.pt, twt<T>(d), d.twt_tan);
-    C* out2 = fft<T, -1, 0>(o2, r2, 1, d.ph, twh<T>(d), d.twh_tan);
-    C* pb = reinterpret_cast<C*>(d.pbuf);
-    for (int idx = threadIdx.x; idx < 3 * Nh; idx += blockDim.x) {
-        const int c = idx / Nh, j = idx - c * Nh;
-        if (c < 2) {
-            const C cj = out[c * Mt + j];
-            const C cm = out[c * Mt + (j == 0 ? 0 : Mt - j)];
-            C x1, x2;
-            x1.x = (T)0.5 * (cj.x + cm.x); x1.y = (T)0.5 * (cj.y - cm.y);
-            x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
-            pb[(((size_t)(2 * c) * Nr + r) * Mz + q) * Nh + j] = x1;
-            pb[(((size_t)(2 * c + 1) * Nr + r) * Mz + q) * Nh + j] = x2;
-        } else {
-            const C zk = out2[j];
-            const C zm = out2[j == 0 ? 0 : H - j];
-            C ev, od, x;
-            ev.x = (T)0.5 * (zk.x + zm.x); ev.y = (T)0.5 * (zk.y - zm.y);
-            // (Z_k - conj Z_{H-k})/(2i)
-            od.x = (T)0.5 * (zk.y + zm.y); od.y = (T)-0.5 * (zk.x - zm.x);
-            const C t = tr[j];
-            x.x = ev.x + od.x * t.x - od.y * t.y;
-            x.y = ev.y + od.x * t.y + od.y * t.x;
-            pb[(((size_t)4 * Nr + r) * Mz + q) * Nh + j] = x;
-        }
-    }
-}
-
-// Shared memory: three full columns F1..F3 and two half columns H1, H2
-// (4 Mt complex values).  The inverse pair runs in F1/F2 and H1/H2; the
-// products (uu - vv) + i uv and (ww - vv) go to the free buffers and are
-// transformed as a pair, (uw + i vw) into F3, transformed after the first
-// pair's coefficients are written.
-template <typename T>
+// Shared-memory layouts (LAYOUT 5 or 4, in units of Mt complex values):
+//   5: two full and one half column per ping-pong side; the forward pass
+//      transforms (uu - vv) + i uv and (uw + i vw) as one 2-column transform
+//      together with (ww - vv): 10 barrier stages per row for 768 = 3 4^4.
+//   4: three full and two half columns; (uw + i vw) is transformed after the
+//      other two have been written: 15 barrier stages, but 20% less shared
+//      memory, which buys a fourth resident block where 5 Mt does not fit
+//      four (float64 rows with Mt = 768).
+// The launcher picks 5 unless 5 Mt of float64 / float32 values exceeds the
+// four-block budget; the double-float rows always use 5.  With FUSE the full
+// and half-length transforms advance together (one barrier per stage for
+// both); the double-float rows, latency-bound and at a higher register count
+// when fused, run them one after the other.
+template <typename T, int LAYOUT, bool FUSE>
 __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if constexpr (std::is_same<T, dfloat>::value) {
-        rows_5mt<T>(d, smem_raw);
-        return;
-    }
     const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
     const int H = Mt / 2;
     C* F1 = reinterpret_cast<C*>(smem_raw);
-    C* F2 = F1 + Mt;
-    C* F3 = F2 + Mt;
-    C* H1 = F3 + Mt;
-    C* H2 = H1 + H;
+    C *F2, *F3, *H1, *H2;
+    if constexpr (LAYOUT == 5) {            // [F1 (2 Mt) | H1 | F2 (2 Mt) | H2]
+        H1 = F1 + 2 * Mt;
+        F2 = H1 + H;
+        H2 = F2 + 2 * Mt;
+        F3 = nullptr;
+    } else {                                // [F1 | F2 | F3 | H1 | H2]
+        F2 = F1 + Mt;
+        F3 = F2 + Mt;
+        H1 = F3 + Mt;
+        H2 = H1 + H;
+    }
     const int q = blockIdx.x, r = blockIdx.y;
     const C* zb = reinterpret_cast<const C*>(d.zbuf);
     const C* ur = zb + (((size_t)0 * Nr + r) * Mz + q) * Nh;
@@ -686,9 +605,10 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     }
     __syncthreads();
     C *r1, *r2;
-    fft_pair<T, +1>(F1, F2, H1, H2, r1, r2, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
-    C* o1 = (r1 == F1) ? F2 : F1;              // free full buffer
+    fft_pair<T, +1, FUSE>(F1, F2, H1, H2, r1, r2, 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    C* o1 = (r1 == F1) ? F2 : F1;              // free full buffer(s)
     C* o2 = (r2 == H1) ? H2 : H1;              // free half buffer
+    C* p2 = (LAYOUT == 5) ? o1 + Mt : F3;      // where uw + i vw goes
     for (int m = threadIdx.x; m < H; m += blockDim.x) {
         const C w2 = r2[m];
         T bb[2];
@@ -699,7 +619,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
             C b0, b1;
             b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
             b1.x = u * w; b1.y = v * w;          // uw, vw
-            o1[p] = b0; F3[p] = b1;
+            o1[p] = b0; p2[p] = b1;
             bb[e] = w * w - vv;                  // ww - vv
         }
         C z; z.x = bb[0]; z.y = bb[1];
@@ -707,7 +627,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     }
     __syncthreads();
     C *s1, *s3;
-    fft_pair<T, -1>(o1, r1, o2, r2, s1, s3, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    fft_pair<T, -1, FUSE>(o1, r1, o2, r2, s1, s3, LAYOUT == 5 ? 2 : 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
     C* pb = reinterpret_cast<C*>(d.pbuf);
     // unpack two real transforms from one complex transform of length Mt
     auto unpack_full = [&](const C* out, int j, int slot) {
@@ -719,11 +639,12 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         pb[(((size_t)slot * Nr + r) * Mz + q) * Nh + j] = x1;
         pb[(((size_t)(slot + 1) * Nr + r) * Mz + q) * Nh + j] = x2;
     };
-    for (int idx = threadIdx.x; idx < 2 * Nh; idx += blockDim.x) {
-        if (idx < Nh) {
-            unpack_full(s1, idx, 0);                // uu - vv, uv
+    constexpr int NF = (LAYOUT == 5) ? 2 : 1;   // full columns written now
+    for (int idx = threadIdx.x; idx < (NF + 1) * Nh; idx += blockDim.x) {
+        const int c = idx / Nh, j = idx - c * Nh;
+        if (c < NF) {
+            unpack_full(s1 + c * Mt, j, 2 * c);     // uu - vv, uv (and uw, vw)
         } else {
-            const int j = idx - Nh;
             const C zk = s3[j];
             const C zm = s3[j == 0 ? 0 : H - j];
             C ev, od, x;
@@ -736,9 +657,11 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
             pb[(((size_t)4 * Nr + r) * Mz + q) * Nh + j] = x;   // ww - vv
         }
     }
-    // uw + i vw: its ping-pong partner is the full buffer not holding s1
-    C* s2 = fft<T, -1, 0>(F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), d.twt_tan);
-    for (int j = threadIdx.x; j < Nh; j += blockDim.x) unpack_full(s2, j, 2);   // uw, vw
+    if constexpr (LAYOUT == 4) {
+        // uw + i vw: its ping-pong partner is the full buffer not holding s1
+        C* s2 = fft<T, -1, 0>(F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), d.twt_tan);
+        for (int j = threadIdx.x; j < Nh; j += blockDim.x) unpack_full(s2, j, 2);   // uw, vw
+    }
 }
 
 // ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) -----------------
@@ -830,13 +753,23 @@ static bool z_has_odd_primes(const TcDev& d) {
     return false;
 }
 
+// Shared-memory layout of the theta rows (see k_rows): 5 Mt unless that
+// exceeds the budget of four resident blocks (57 KB each) for float64 or
+// float32 values.
+template <typename T>
+static int rows_layout(const TcDev& d) {
+    typedef typename V2<T>::t C;
+    if (std::is_same<T, dfloat>::value) return 5;
+    return 5 * (size_t)d.Mt * sizeof(C) <= 57 * 1024 ? 5 : 4;
+}
+
 template <typename T>
 static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles) {
     typedef typename V2<T>::t C;
     const int ct = d.ztile;
     const size_t smz = 2 * (size_t)ct * d.Mz * sizeof(C);
-    // 3 full + 2 half columns (double-float: 2 x (2 full + 1 half))
-    const size_t smr = (std::is_same<T, dfloat>::value ? 5 : 4) * (size_t)d.Mt * sizeof(C);
+    const int layout = rows_layout<T>(d);
+    const size_t smr = (size_t)layout * d.Mt * sizeof(C);
     const bool odd = z_has_odd_primes(d);
     const bool tan = std::is_same<T, double>::value && d.zfam0;
     if (which == 0) {
@@ -845,7 +778,9 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
         else if (tan) k_zinv<double, 0><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
         else k_zinv<T, 1><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
     } else if (which == 1) {
-        k_rows<T><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
+        constexpr bool fuse = !std::is_same<T, dfloat>::value;
+        if (layout == 5) k_rows<T, 5, fuse><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
+        else k_rows<T, 4, fuse><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
     } else {
         const dim3 g(ntiles, d.Nr, TC_NPROD);
         if (odd) k_zfwd<T, 2><<<g, 256, smz, s>>>(d, tile0);
@@ -892,7 +827,9 @@ cudaError_t tc_set_kernel_attributes() {
     set((const void*)k_zinv<double, 2>); set((const void*)k_zinv<float, 2>); set((const void*)k_zinv<dfloat, 2>);
     set((const void*)k_zfwd<double, 1>); set((const void*)k_zfwd<float, 1>); set((const void*)k_zfwd<dfloat, 1>);
     set((const void*)k_zfwd<double, 2>); set((const void*)k_zfwd<float, 2>); set((const void*)k_zfwd<dfloat, 2>);
-    set((const void*)k_rows<double>); set((const void*)k_rows<float>); set((const void*)k_rows<dfloat>);
+    set((const void*)k_rows<double, 5, true>); set((const void*)k_rows<float, 5, true>);
+    set((const void*)k_rows<double, 4, true>); set((const void*)k_rows<float, 4, true>);
+    set((const void*)k_rows<dfloat, 5, false>); set((const void*)k_rows<dfloat, 4, false>);
     set((const void*)k_zinv<double, 0>); set((const void*)k_zfwd<double, 0>);
     set((const void*)k_rows_phys);
     return e;
