@@ -152,6 +152,23 @@ int tc_set_field(tc_handle* h, int which, const void* host_buf, size_t bytes);
 /* Bytes of one field in the given space. */
 size_t tc_field_bytes(const tc_handle* h, int which, int space);
 
+/* Checkpoint / resume (the paper saves fields every 10 time units, Sec. 4;
+ * here the whole time-stepping state is saved, so that a resumed run is bit
+ * for bit the run that was not interrupted):
+ *   tc_state_bytes: size of a state image of this case;
+ *   tc_save_state:  writes the image into the caller's host buffer: a header
+ *                   (shape, time, step count, RK phase) and, as float64, v,
+ *                   eta, u, w and the RK memories H_v, H_eta ([Nr][Nz][Ntheta/2]
+ *                   complex128 each), then U, W and their RK memories ([Nr]);
+ *   tc_load_state:  restores an image saved from a case of the same Nr,
+ *                   Ntheta and Nz (any precision form and tiles); TC_ERR_SIZE
+ *                   for a wrong size, TC_ERR_ARG for another shape or a
+ *                   damaged header.
+ * Both are synchronous and must not overlap a step in flight. */
+size_t tc_state_bytes(const tc_handle* h);
+int tc_save_state(tc_handle* h, void* host_buf, size_t bytes);
+int tc_load_state(tc_handle* h, const void* host_buf, size_t bytes);
+
 /* Torque, friction Reynolds numbers, kinetic energy, viscous dissipation
  * and wall power of the current state (synchronous on the handle's stream;
  * uses the handle's transform scratch, so not while a step is in flight). */

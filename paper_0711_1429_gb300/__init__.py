@@ -90,6 +90,12 @@ def lib():
     L.tc_torque_stats.argtypes = [vp, ctypes.POINTER(tc_stats)]
     L.tc_set_stream.restype = i
     L.tc_set_stream.argtypes = [vp, vp]
+    L.tc_state_bytes.restype = sz
+    L.tc_state_bytes.argtypes = [vp]
+    L.tc_save_state.restype = i
+    L.tc_save_state.argtypes = [vp, vp, sz]
+    L.tc_load_state.restype = i
+    L.tc_load_state.argtypes = [vp, vp, sz]
     L.tc_set_tiles.restype = i
     L.tc_set_tiles.argtypes = [vp, i, i, i]
     L.tc_get_tiles.restype = i
@@ -232,6 +238,19 @@ def tc_torque_stats(h):
 
 def tc_set_stream(h, stream_ptr):
     return _check(lib().tc_set_stream(h, stream_ptr))
+
+
+def tc_save_state(h):
+    """The whole time-stepping state as a bytes object (see tc.h)."""
+    n = lib().tc_state_bytes(h)
+    buf = ctypes.create_string_buffer(n)
+    _check(lib().tc_save_state(h, buf, n))
+    return buf.raw
+
+
+def tc_load_state(h, image):
+    buf = ctypes.create_string_buffer(image, len(image))
+    return _check(lib().tc_load_state(h, buf, len(image)))
 
 
 LINE_VARIANTS = (64, 128, 256, 1003, 1004, 2007)

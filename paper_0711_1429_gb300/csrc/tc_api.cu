@@ -908,6 +908,80 @@ int tc_step(tc_handle* h, int nsteps) {
     return check_flags(h);
 }
 
+// State image: header, then v, eta, u, w, Hv, He (Nr * npairs complex128
+// each), then U, W, HU, HW (Nr float64 each).
+namespace {
+struct StateHeader {
+    char magic[8];                 // "TCSTATE1"
+    int Nr, Ntheta, Nz, phase;
+    long long step;
+    double t;
+};
+}  // namespace
+
+size_t tc_state_bytes(const tc_handle* h) {
+    if (!h) return 0;
+    const size_t P1 = (size_t)h->d.Nr * h->d.npairs;
+    return sizeof(StateHeader) + 6 * P1 * sizeof(double2) + 4 * (size_t)h->d.Nr * sizeof(double);
+}
+
+int tc_save_state(tc_handle* h, void* buf, size_t bytes) {
+    if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
+    if (bytes != tc_state_bytes(h)) { set_err("state buffer size " + std::to_string(bytes) + " != " + std::to_string(tc_state_bytes(h))); return TC_ERR_SIZE; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    TcDev& d = h->d;
+    StateHeader hd;
+    std::memcpy(hd.magic, "TCSTATE1", 8);
+    hd.Nr = d.Nr; hd.Ntheta = 2 * d.Nh; hd.Nz = d.Nz; hd.phase = h->phase;
+    hd.step = h->step; hd.t = h->t;
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const size_t F = (size_t)d.Nr * d.npairs * sizeof(double2);
+    for (const double2* f : {d.v, d.eta, d.u, d.w, d.Hv, d.He}) {
+        CK(cudaMemcpyAsync(p, f, F, cudaMemcpyDeviceToHost, h->stream));
+        p += F;
+    }
+    const size_t M = (size_t)d.Nr * sizeof(double);
+    for (const double* f : {d.U, d.W, d.HU, d.HW}) {
+        CK(cudaMemcpyAsync(p, f, M, cudaMemcpyDeviceToHost, h->stream));
+        p += M;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return TC_OK;
+}
+
+int tc_load_state(tc_handle* h, const void* buf, size_t bytes) {
+    if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
+    if (bytes != tc_state_bytes(h)) { set_err("state buffer size " + std::to_string(bytes) + " != " + std::to_string(tc_state_bytes(h))); return TC_ERR_SIZE; }
+    TcDev& d = h->d;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "TCSTATE1", 8) != 0 || hd.Nr != d.Nr || hd.Ntheta != 2 * d.Nh || hd.Nz != d.Nz ||
+        hd.phase < 0 || hd.phase > 2) {
+        set_err("state image of another shape, or a damaged header");
+        return TC_ERR_ARG;
+    }
+    const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof(hd);
+    const size_t F = (size_t)d.Nr * d.npairs * sizeof(double2);
+    for (double2* f : {d.v, d.eta, d.u, d.w, d.Hv, d.He}) {
+        CK(cudaMemcpyAsync(f, p, F, cudaMemcpyHostToDevice, h->stream));
+        p += F;
+    }
+    const size_t M = (size_t)d.Nr * sizeof(double);
+    for (double* f : {d.U, d.W, d.HU, d.HW}) {
+        CK(cudaMemcpyAsync(f, p, M, cudaMemcpyHostToDevice, h->stream));
+        p += M;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->need_init = false;            // the image holds the RK memories and u, w
+    h->phase = hd.phase;
+    h->step = hd.step;
+    h->t = hd.t;
+    return TC_OK;
+}
+
 size_t tc_field_bytes(const tc_handle* h, int which, int space) {
     if (!h) return 0;
     const TcDev& d = h->d;

@@ -435,3 +435,77 @@ def test_launch_shapes_change_no_bits(precision):
                 tc.tc_set_tiles(h, *bad)
     finally:
         tc.tc_destroy(h)
+
+
+def test_checkpoint_resume_is_bit_identical():
+    """A run saved after 5 steps (and after a further substep) and resumed in
+    a fresh handle ends bit for bit where the uninterrupted run ends; images
+    of another shape or size are refused."""
+    cfg = dict(Nr=33, Ntheta=32, Nz=24, zeta=0.8, Re_i=600.0, Re_o=-50.0, dt=2e-3)
+    v, e = inputs(33, 32, 24, 0.8, 13, "k2", 0.05)
+    mk = lambda prec=tc.TC_PREC_FP64: gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"],
+                                               cfg["Re_o"], cfg["dt"], v=v, eta=e, precision=prec)
+    a, b, c = mk(), mk(), mk()
+    try:
+        tc.tc_step(a, 5)
+        img = tc.tc_save_state(a)
+        tc.tc_advance_substeps(a, 1)
+        img_mid = tc.tc_save_state(a)
+        tc.tc_advance_substeps(a, 2)
+        tc.tc_step(a, 4)
+        tc.tc_load_state(b, img)
+        tc.tc_step(b, 5)
+        tc.tc_load_state(c, img_mid)
+        tc.tc_advance_substeps(c, 2)
+        tc.tc_step(c, 4)
+        ga = gpu_state(a, 33, 24, 16)
+        for h in (b, c):
+            g = gpu_state(h, 33, 24, 16)
+            for k in ga:
+                assert np.array_equal(g[k], ga[k]), k
+        sa, sb = tc.tc_torque_stats(a), tc.tc_torque_stats(b)
+        assert abs(sa.pop("t") - sb.pop("t")) < 1e-15     # summed in another order
+        assert sa == sb and sa["step"] == 10
+        with pytest.raises(tc.TcError) as ex:
+            tc.tc_load_state(b, img[:-8])
+        assert ex.value.code == tc.TC_ERR_SIZE
+        bad = bytearray(img)
+        bad[0:8] = b"XXXXXXXX"
+        with pytest.raises(tc.TcError) as ex:
+            tc.tc_load_state(b, bytes(bad))
+        assert ex.value.code == tc.TC_ERR_ARG
+    finally:
+        for h in (a, b, c):
+            tc.tc_destroy(h)
+    # another shape: refused
+    h = gpu_case(33, 32, 32, 0.8, 600.0, -50.0, 2e-3)
+    try:
+        with pytest.raises(tc.TcError):
+            tc.tc_load_state(h, img)
+    finally:
+        tc.tc_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["tc-129x128x128", "tc-257x512x512"])
+def test_physical_transform_matches_cufft(name):
+    """The z and theta transforms against cuFFT (torch.fft on the device):
+    the physical field u(theta_p, z_q) = sum u^ exp(i(m theta_p + alpha z_q))
+    of tc_get_field(PHYSICAL) equals irfft2 of the zero-padded spectrum."""
+    torch = pytest.importorskip("torch")
+    from paper_0711_1429_gb300.synthetic import WORKLOADS
+    w = WORKLOADS[name]
+    Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
+    Nh, Mt, Mz = Nt // 2, 3 * Nt // 2, 3 * Nz // 2
+    v, e = workload_inputs(name)
+    h = gpu_case(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], v=v, eta=e)
+    try:
+        tc.tc_step(h, 1)
+        spec = torch.from_numpy(tc.tc_get_field(h, tc.TC_FIELD_U).reshape(Nr, Nz, Nh)).cuda()
+        phys = tc.tc_get_field(h, tc.TC_FIELD_U, tc.TC_PHYSICAL).reshape(Nr, Mz, Mt)
+    finally:
+        tc.tc_destroy(h)
+    X = torch.zeros((Nr, Mz, Mt // 2 + 1), dtype=torch.complex128, device="cuda")
+    X[:, :Nz // 2, :Nh] = spec[:, :Nz // 2, :]
+    X[:, Mz - Nz // 2 + 1:, :Nh] = spec[:, Nz // 2 + 1:, :]
+    ref = (torch.fft.irfft2(X, s=(Mz, Mt)) * (Mz * Mt)).cpu().numpy()
+    assert relerr(phys, ref) < 1e-12
