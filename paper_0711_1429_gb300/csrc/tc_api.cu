@@ -877,6 +877,7 @@ int tune_chunks(tc_handle* h, int nsteps, int* done) {
 extern "C" {
 
 int tc_advance_substeps(tc_handle* h, int nsub) {
+    tcx::Range nvtx_range("tc_advance_substeps");
     if (!h || nsub < 0) { set_err("invalid handle or substep count"); return TC_ERR_ARG; }
     int rc;
     if ((rc = ensure_init(h))) return rc;
@@ -894,6 +895,7 @@ int tc_advance_substeps(tc_handle* h, int nsub) {
 }
 
 int tc_step(tc_handle* h, int nsteps) {
+    tcx::Range nvtx_range("tc_step");
     if (!h || nsteps < 0) { set_err("invalid handle or step count"); return TC_ERR_ARG; }
     if (h->phase != 0) { set_err("tc_step called inside a step; finish it with tc_advance_substeps"); return TC_ERR_ARG; }
     int rc;
@@ -926,6 +928,7 @@ size_t tc_state_bytes(const tc_handle* h) {
 }
 
 int tc_save_state(tc_handle* h, void* buf, size_t bytes) {
+    tcx::Range nvtx_range("tc_save_state");
     if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
     if (bytes != tc_state_bytes(h)) { set_err("state buffer size " + std::to_string(bytes) + " != " + std::to_string(tc_state_bytes(h))); return TC_ERR_SIZE; }
     int rc;
@@ -953,6 +956,7 @@ int tc_save_state(tc_handle* h, void* buf, size_t bytes) {
 }
 
 int tc_load_state(tc_handle* h, const void* buf, size_t bytes) {
+    tcx::Range nvtx_range("tc_load_state");
     if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
     if (bytes != tc_state_bytes(h)) { set_err("state buffer size " + std::to_string(bytes) + " != " + std::to_string(tc_state_bytes(h))); return TC_ERR_SIZE; }
     TcDev& d = h->d;
@@ -992,6 +996,7 @@ size_t tc_field_bytes(const tc_handle* h, int which, int space) {
 }
 
 int tc_get_field(tc_handle* h, int which, int space, void* buf, size_t bytes) {
+    tcx::Range nvtx_range("tc_get_field");
     if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
     if (which < 0 || which > TC_FIELD_MEAN_W || (space != TC_SPECTRAL && space != TC_PHYSICAL)) {
         set_err("unknown field or space");
@@ -1026,6 +1031,7 @@ int tc_get_field(tc_handle* h, int which, int space, void* buf, size_t bytes) {
 }
 
 int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
+    tcx::Range nvtx_range("tc_set_field");
     if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
     TcDev& d = h->d;
     if (which == TC_FIELD_MEAN_U || which == TC_FIELD_MEAN_W) {
@@ -1051,6 +1057,7 @@ int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
 }
 
 int tc_torque_stats(tc_handle* h, tc_stats* out) {
+    tcx::Range nvtx_range("tc_torque_stats");
     if (!h || !out) { set_err("null handle or output"); return TC_ERR_ARG; }
     int rc;
     if ((rc = ensure_init(h))) return rc;
@@ -1103,6 +1110,7 @@ int tc_torque_stats(tc_handle* h, tc_stats* out) {
 size_t tc_device_bytes(const tc_handle* h) { return h ? h->dev_bytes : 0; }
 
 int tc_phase_times(tc_handle* h, int nsteps, double* ms, int nphases) {
+    tcx::Range nvtx_range("tc_phase_times");
     if (!h || nsteps < 1 || !ms || nphases < TC_NPHASES) { set_err("invalid arguments"); return TC_ERR_ARG; }
     if (h->phase != 0) { set_err("tc_phase_times called inside a step"); return TC_ERR_ARG; }
     int rc;

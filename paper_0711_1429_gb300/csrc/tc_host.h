@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "tc_internal.h"
+#include <nvtx3/nvToolsExt.h>
 #include "../../include/tc.h"
 
 struct HostStencils {
@@ -42,6 +43,12 @@ struct tc_handle {
 };
 
 namespace tcx {
+// NVTX range over one API call (visible in Nsight timelines; free without a
+// tool attached)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 void set_err(const std::string& s);
 int ensure_init(tc_handle* h);                 // H_1 and u, w of the current state
 void launch_step(tc_handle* h, cudaStream_t s);  // the 15 kernels of one step
