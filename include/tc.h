@@ -66,9 +66,10 @@ enum { TC_SPECTRAL = 0, TC_PHYSICAL = 1 };
 
 enum {
     TC_PREC_FP64 = 0,       /* every step in float64 */
-    TC_PREC_MIXED = 1,      /* FFTs and products in float32; radial rows,
-                               banded solves, continuity and the mean mode in
-                               float64 */
+    TC_PREC_MIXED = 1,      /* FFTs, products and explicit radial rows in
+                               float32, their continuity term in double-float;
+                               banded solves, RK memory, reconstruction and
+                               the mean mode in float64 */
     TC_PREC_DF64 = 2        /* FFTs and products in double-float arithmetic
                                (pairs of float32, ~48 significand bits) on the
                                float32 pipe; everything else as TC_PREC_FP64 */
@@ -83,12 +84,15 @@ typedef struct {
     double Theta;           /* azimuthal box (radians); <= 0: L_theta = 10 pi h
                                at the centreline (Sec. 4)                      */
     double Lz;              /* axial box in h; <= 0: 5 h (Sec. 4)              */
-    int precision;          /* TC_PREC_FP64 or TC_PREC_MIXED                  */
+    int precision;          /* TC_PREC_FP64, TC_PREC_MIXED or TC_PREC_DF64     */
     int device;             /* CUDA device ordinal; < 0: current device        */
     int autotune;           /* 1: time the candidate tile shapes of the z
-                               transforms and the line-phase block size at
-                               creation and keep the fastest (cached per shape
-                               class); results do not depend on the choice     */
+                               transforms and the line-kernel variants at
+                               creation, and the column groups of the step
+                               graph (1 or 2) on the first tc_step of three or
+                               more steps, keeping the fastest (cached per
+                               shape class); results do not depend on the
+                               choices                                         */
     double stretch;         /* radial grid: 0 uniform; a > 0 the tanh map
                                r_j = (R_i + 1) + tanh(a s_j)/tanh(a),
                                s_j = -1 + 2j/(Nr-1), denser at both walls (the
