@@ -70,9 +70,11 @@ enum {
                                float32, their continuity term in double-float;
                                banded solves, RK memory, reconstruction and
                                the mean mode in float64 */
-    TC_PREC_DF64 = 2        /* FFTs and products in double-float arithmetic
-                               (pairs of float32, ~48 significand bits) on the
-                               float32 pipe; everything else as TC_PREC_FP64 */
+    TC_PREC_DF64 = 2        /* FFTs, products and explicit radial rows in
+                               double-float arithmetic (pairs of float32, ~48
+                               significand bits) on the float32 pipe; solves,
+                               RK memory, reconstruction and the mean mode in
+                               float64 */
 };
 
 typedef struct {
