@@ -286,6 +286,13 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False)
                "torque": torque}
 
 
+# DRAM bytes per z row of k_rows<double> (Ntheta = 512, Mt = 768): one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on
+# the paper workload 129 x 512 x 170, 32895 rows per launch; the per-row
+# traffic does not depend on Nr or Nz.
+ROWS_FP64_BYTES_PER_ROW = {512: (404993280 + 627219200) / 32895}
+
+
 def roofline_of(w, prec_name, ph, peaks):
     alg = algorithmic(w, prec_name)
     dom = max(ph, key=ph.get)
@@ -309,6 +316,10 @@ def roofline_of(w, prec_name, ph, peaks):
                 "frac": (a["bytes"] / t / 1e9 / hbm) if hbm else None, "traffic": None,
                 "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)",
                 "note": "the line kernel is float64-issue-bound (ncu); bytes/time is reported against HBM"}
+    if dom == "theta_rows_products" and prec_name == "fp64" and w["Ntheta"] in ROWS_FP64_BYTES_PER_ROW:
+        rows = w["Nr"] * 3 * w["Nz"] // 2
+        roof["traffic"] = ROWS_FP64_BYTES_PER_ROW[w["Ntheta"]] * rows
+        roof["traffic_source"] = "ncu dram bytes per row of the same kernel on paper-129x512x170, scaled by rows"
     roof["phase_ms"] = ph
     return roof
 
