@@ -514,6 +514,15 @@ int init_handle(tc_handle* h) {
             std::vector<double> c = tangent_twiddles(d.pz0);
             if (!c.empty()) {
                 if ((rc_ = upload(h, d.twz_tan, c))) return rc_;
+                std::vector<float2> f0(r0.size() ? r0.size() : 1, make_float2(1.0f, 0.0f));
+                std::vector<float4> x0(r0.size() ? r0.size() : 1, make_float4(1.0f, 0.0f, 0.0f, 0.0f));
+                for (size_t i = 0; i < r0.size(); ++i) {
+                    const float rh = (float)r0[i], ih = (float)i0[i];
+                    f0[i] = make_float2(rh, ih);
+                    x0[i] = make_float4(rh, (float)(r0[i] - (ld)rh), ih, (float)(i0[i] - (ld)ih));
+                }
+                if ((rc_ = upload(h, d.twz0_f, f0))) return rc_;
+                if ((rc_ = upload(h, d.twz0_x, x0))) return rc_;
                 d.zfam0 = 1;
             }
         }

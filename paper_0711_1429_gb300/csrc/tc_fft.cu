@@ -469,10 +469,19 @@ __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename 
     b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
 }
 
+// z twiddles of the plan the kernel runs: pz (family 1) or pz0 (family 0;
+// float64 reads the tangent table instead and never this one)
+template <typename T, int ZF> __device__ __forceinline__ const typename V2<T>::t* twz_of(const TcDev& d);
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twz(const TcDev& d);
 template <> __device__ __forceinline__ const dcomplex* twz<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twz_x); }
 template <> __device__ __forceinline__ const double2* twz<double>(const TcDev& d) { return d.twz_d; }
 template <> __device__ __forceinline__ const float2* twz<float>(const TcDev& d) { return d.twz_f; }
+template <typename T, int ZF> __device__ __forceinline__ const typename V2<T>::t* twz_of(const TcDev& d) {
+    if constexpr (ZF != 0) return twz<T>(d);
+    else if constexpr (std::is_same<T, float>::value) return d.twz0_f;
+    else if constexpr (std::is_same<T, dfloat>::value) return reinterpret_cast<const dcomplex*>(d.twz0_x);
+    else return twz<T>(d);
+}
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twt(const TcDev& d);
 template <> __device__ __forceinline__ const dcomplex* twt<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twt_x); }
 template <> __device__ __forceinline__ const double2* twt<double>(const TcDev& d) { return d.twt_d; }
@@ -518,7 +527,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz<T>(d), d.twz_tan);
+    C* res = fft<T, +1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
@@ -682,7 +691,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
-    C* res = fft<T, -1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz<T>(d), d.twz_tan);
+    C* res = fft<T, -1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
     T scale;
     if constexpr (std::is_same<T, double>::value) scale = d.fscale;
     else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;
@@ -771,11 +780,13 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
     const int layout = rows_layout<T>(d);
     const size_t smr = (size_t)layout * d.Mt * sizeof(C);
     const bool odd = z_has_odd_primes(d);
-    const bool tan = std::is_same<T, double>::value && d.zfam0;
+    // the radix-3/4/2 plan pz0 (tangent twiddles in float64) when the axial
+    // length has a compile-time plan, else radix 16 or the prime stages
+    const bool fam0 = d.zfam0 != 0;
     if (which == 0) {
         const dim3 g(ntiles, d.Nr, 3);
         if (odd) k_zinv<T, 2><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
-        else if (tan) k_zinv<double, 0><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
+        else if (fam0) k_zinv<T, 0><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
         else k_zinv<T, 1><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
     } else if (which == 1) {
         constexpr bool fuse = !std::is_same<T, dfloat>::value;
@@ -784,7 +795,7 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
     } else {
         const dim3 g(ntiles, d.Nr, TC_NPROD);
         if (odd) k_zfwd<T, 2><<<g, 256, smz, s>>>(d, tile0);
-        else if (tan) k_zfwd<double, 0><<<g, 256, smz, s>>>(d, tile0);
+        else if (fam0) k_zfwd<T, 0><<<g, 256, smz, s>>>(d, tile0);
         else k_zfwd<T, 1><<<g, 256, smz, s>>>(d, tile0);
     }
 }
@@ -831,6 +842,8 @@ cudaError_t tc_set_kernel_attributes() {
     set((const void*)k_rows<double, 4, true>); set((const void*)k_rows<float, 4, true>);
     set((const void*)k_rows<dfloat, 5, false>); set((const void*)k_rows<dfloat, 4, false>);
     set((const void*)k_zinv<double, 0>); set((const void*)k_zfwd<double, 0>);
+    set((const void*)k_zinv<float, 0>); set((const void*)k_zfwd<float, 0>);
+    set((const void*)k_zinv<dfloat, 0>); set((const void*)k_zfwd<dfloat, 0>);
     set((const void*)k_rows_phys);
     return e;
 }

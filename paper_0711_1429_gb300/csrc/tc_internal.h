@@ -87,6 +87,10 @@ struct TcDev {
     int zfam0;
     FftPlan pz0;
     const double* twz_tan;
+    // twiddles of the plan pz0 in the plain (cos, sin) form for the float32
+    // and double-float z transforms, which use that plan too
+    const float2* twz0_f;
+    const float4* twz0_x;
     const double2* twz_d;
     const double2* twt_d;
     const double2* twh_d;
