@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc.so")
-SOURCES = ["tc_api.cu", "tc_fft.cu", "tc_line.cu", "tc_peak.cu", "tc_noalloc.cu", "tc_serve.cu"]
+SOURCES = ["tc_fft_f64.cu", "tc_fft_df.cu", "tc_fft_f32.cu", "tc_line.cu", "tc_api.cu", "tc_fft.cu",
+           "tc_peak.cu", "tc_noalloc.cu", "tc_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-Xptxas", "-O3"]

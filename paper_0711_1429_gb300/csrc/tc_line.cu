@@ -46,7 +46,6 @@ __device__ __forceinline__ Coef coef_at(double r, double rinv, double m, double 
 
 __device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 // (i s) * a
 __device__ __forceinline__ double2 cimag(double s, double2 a) { return make_double2(-s * a.y, s * a.x); }
