@@ -43,6 +43,10 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.tc_get_field(None, 0, 0, None, 0) == tc.TC_ERR_ARG
     assert lib.tc_field_bytes(None, 0, 0) == 0
     assert lib.tc_set_tiles(None, 4, 128, 1) == tc.TC_ERR_ARG
+    assert lib.tc_get_tiles(None, None, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_state_bytes(None) == 0
+    assert lib.tc_save_state(None, None, 0) == tc.TC_ERR_ARG
+    assert lib.tc_load_state(None, None, 0) == tc.TC_ERR_ARG
     lib.tc_destroy(None)
 
 
