@@ -606,23 +606,37 @@ int ensure_init(tc_handle* h) {
 
 int prepare_pipeline(tc_handle* h) {
     if (h->pipe_ready) return TC_OK;
-    for (auto& st : h->aux) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    // on a failure, whatever was created is released again
+    cudaError_t e = cudaSuccess;
+    for (auto& st : h->aux)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     for (int c = 0; c < TC_MAX_CHUNKS; ++c) {
-        CK(cudaEventCreateWithFlags(&h->evz[c], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->evl[c], cudaEventDisableTiming));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evz[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evl[c], cudaEventDisableTiming);
     }
-    CK(cudaEventCreateWithFlags(&h->evm, cudaEventDisableTiming));
-    for (auto& e : h->evj) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    h->pipe_ready = true;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evm, cudaEventDisableTiming);
+    for (auto& ev : h->evj)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    h->pipe_ready = true;                // lets release_pipeline free what exists
+    if (e != cudaSuccess) {
+        release_pipeline(h);
+        set_err(std::string("pipeline streams and events: ") + cudaGetErrorString(e));
+        return TC_ERR_CUDA;
+    }
     return TC_OK;
 }
 
 void release_pipeline(tc_handle* h) {
     if (!h->pipe_ready) return;
-    for (auto& st : h->aux) { cudaStreamDestroy(st); st = nullptr; }
-    for (int c = 0; c < TC_MAX_CHUNKS; ++c) { cudaEventDestroy(h->evz[c]); cudaEventDestroy(h->evl[c]); }
-    cudaEventDestroy(h->evm);
-    for (auto& e : h->evj) cudaEventDestroy(e);
+    for (auto& st : h->aux) { if (st) cudaStreamDestroy(st); st = nullptr; }
+    for (int c = 0; c < TC_MAX_CHUNKS; ++c) {
+        if (h->evz[c]) cudaEventDestroy(h->evz[c]);
+        if (h->evl[c]) cudaEventDestroy(h->evl[c]);
+        h->evz[c] = h->evl[c] = nullptr;
+    }
+    if (h->evm) cudaEventDestroy(h->evm);
+    h->evm = nullptr;
+    for (auto& ev : h->evj) { if (ev) cudaEventDestroy(ev); ev = nullptr; }
     h->pipe_ready = false;
 }
 
@@ -853,7 +867,11 @@ int tune_chunks(tc_handle* h, int nsteps, int* done) {
     }
     if (!tcx::chunks_valid(h, 2)) { h->chunks_auto = 1; return TC_OK; }
     if (nsteps < 3) return TC_OK;              // decide on a later, longer call
-    cudaEvent_t a, b;
+    cudaEvent_t a = nullptr, b = nullptr;
+    struct Events {                      // destroyed on every exit
+        cudaEvent_t *a, *b;
+        ~Events() { if (*a) cudaEventDestroy(*a); if (*b) cudaEventDestroy(*b); }
+    } guard{&a, &b};
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     float best = 1e30f;
@@ -862,7 +880,7 @@ int tune_chunks(tc_handle* h, int nsteps, int* done) {
         h->chunks_auto = c;
         if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
         int rc = ensure_graph(h);
-        if (rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
+        if (rc) return rc;
         CK(cudaGraphUpload(h->graph, h->stream));
         CK(cudaEventRecord(a, h->stream));
         CK(cudaGraphLaunch(h->graph, h->stream));
@@ -873,8 +891,6 @@ int tune_chunks(tc_handle* h, int nsteps, int* done) {
         if (ms < best) { best = ms; bestc = c; }
         ++*done;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     h->chunks_auto = bestc;
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     std::lock_guard<std::mutex> lk(g_tune_mu);
