@@ -353,7 +353,24 @@ __host__ __device__ constexpr int plan_tan_off(int M, int s) {
     return o;
 }
 
-template <typename T, int SIGN, int M, int F, int S>
+// First radix-3 stage (Ns = 1, no twiddles) of an inverse transform whose
+// input is a spectrum zero-padded by the 3/2 rule: input j + M/3 lies in the
+// zero band for every j < M/3, so the butterfly skips it.  With v1 = 0 the
+// radix-3 sums are bit for bit those of the full butterfly.
+template <int SIGN, typename T, typename C>
+__device__ __forceinline__ void stockham_bfly3_zero_mid(const C* sc, C* dcol, int j, int nb) {
+    const T h = (T)0.5;
+    const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
+    const C v0 = sc[j], v2 = sc[j + 2 * nb];
+    C t0; t0.x = v0.x - h * v2.x; t0.y = v0.y - h * v2.y;
+    C id = c_si<SIGN>(v2); id.x *= s3; id.y *= s3;   // SIGN i s3 v2 = -(SIGN i s3 (0 - v2))
+    C* dc = dcol + 3 * j;
+    dc[0] = c_add(v0, v2);
+    dc[1] = c_sub(t0, id);
+    dc[2] = c_add(t0, id);
+}
+
+template <typename T, int SIGN, int M, int F, int S, bool Z0 = false>
 __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t* src, typename V2<T>::t* dst,
                                                               int ncols, const typename V2<T>::t* __restrict__ tw,
                                                               const double* __restrict__ twtan) {
@@ -368,13 +385,15 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
         for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
             const int col = b / nb;
             const int j = b - col * nb;
-            if constexpr (std::is_same<T, double>::value && F == 0 && Ns > 1)
+            if constexpr (Z0 && S == 0 && R == 3)
+                stockham_bfly3_zero_mid<SIGN, T>(src + col * M, dst + col * M, j, nb);
+            else if constexpr (std::is_same<T, double>::value && F == 0 && Ns > 1)
                 stockham_bfly_tan<R, SIGN>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S));
             else
                 stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
         }
         __syncthreads();
-        return fft_fixed_stage<T, SIGN, M, F, S + 1>(dst, src, ncols, tw, twtan);
+        return fft_fixed_stage<T, SIGN, M, F, S + 1, Z0>(dst, src, ncols, tw, twtan);
     }
 }
 
@@ -382,11 +401,13 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
 // Dispatch on the transform length: compile-time plans for the lengths of
 // the supported grids (those of tc_fft_fixed_length), the run-time plan
 // otherwise (same arithmetic).
-template <typename T, int SIGN, int F>
+// Z0: the input is a 3/2-padded spectrum (middle third zero), which the
+// first stage of the compile-time plans skips.
+template <typename T, int SIGN, int F, bool Z0 = false>
 __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw,
                                   const double* __restrict__ twtan = nullptr) {
-#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0>(buf0, buf1, ncols, tw, twtan);
+#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0, Z0>(buf0, buf1, ncols, tw, twtan);
     if constexpr (F == 2) {
         return fft_stockham<T, SIGN, 2>(buf0, buf1, ncols, pl, tw);
     } else {
@@ -404,19 +425,21 @@ __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* bu
 // half length M2) advanced stage by stage in one loop, one barrier per
 // stage for both; each keeps its own plan, twiddles and ping-pong pair.  On
 // return a_res / b_res hold the buffers with the results.
-template <typename T, int SIGN, int M, int S>
+template <typename T, int SIGN, int M, int S, bool Z0 = false>
 __device__ __forceinline__ void pair_bfly(typename V2<T>::t* src, typename V2<T>::t* dst, int j,
                                           const typename V2<T>::t* __restrict__ tw,
                                           const double* __restrict__ twtan) {
     constexpr int R = plan_radix_f(M, S, 0);
     constexpr int Ns = plan_ns_f(M, S, 0);
     constexpr int nb = M / R;
-    if constexpr (std::is_same<T, double>::value && Ns > 1)
+    if constexpr (Z0 && S == 0 && R == 3)
+        stockham_bfly3_zero_mid<SIGN, T>(src, dst, j, nb);
+    else if constexpr (std::is_same<T, double>::value && Ns > 1)
         stockham_bfly_tan<R, SIGN>(src, dst, j, nb, Ns, twtan + plan_tan_off(M, S));
     else
         stockham_bfly<R, SIGN, T>(src, dst, j, nb, Ns, tw + plan_off_f(M, S, 0));
 }
-template <typename T, int SIGN, int M1, int M2, int S>
+template <typename T, int SIGN, int M1, int M2, int S, bool Z0A = false>
 __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V2<T>::t* a1,
                                                typename V2<T>::t* b0, typename V2<T>::t* b1,
                                                typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
@@ -435,26 +458,26 @@ __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V
             if constexpr (A) {
                 if (b < nA) {
                     const int col = b / nb1;
-                    pair_bfly<T, SIGN, M1, (A ? S : 0)>(a0 + col * M1, a1 + col * M1, b - col * nb1, tw1, tt1);
+                    pair_bfly<T, SIGN, M1, (A ? S : 0), Z0A>(a0 + col * M1, a1 + col * M1, b - col * nb1, tw1, tt1);
                     continue;
                 }
             }
             if constexpr (B) pair_bfly<T, SIGN, M2, (B ? S : 0)>(b0, b1, b - nA, tw2, tt2);
         }
         __syncthreads();
-        fft_pair_stage<T, SIGN, M1, M2, S + 1>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
-                                               a_res, b_res, na, tw1, tt1, tw2, tt2);
+        fft_pair_stage<T, SIGN, M1, M2, S + 1, Z0A>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
+                                                    a_res, b_res, na, tw1, tt1, tw2, tt2);
     }
 }
 // Full-length (plan p1, na contiguous columns) and half-length (plan p2,
 // one column) transforms together when FUSE is set and both lengths have
 // compile-time plans, else one after the other.
-template <typename T, int SIGN, bool FUSE>
+template <typename T, int SIGN, bool FUSE, bool Z0A = false>
 __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename V2<T>::t* b0, typename V2<T>::t* b1,
                          typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                          const FftPlan& p1, const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
                          const FftPlan& p2, const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
-#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0>(a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
+#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0, Z0A>(a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
     if constexpr (FUSE) {
         switch (p1.M) {
             TC_PAIR_CASE(24) TC_PAIR_CASE(36) TC_PAIR_CASE(48) TC_PAIR_CASE(72) TC_PAIR_CASE(96)
@@ -464,7 +487,7 @@ __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename 
         }
     }
 #undef TC_PAIR_CASE
-    a_res = fft<T, SIGN, 0>(a0, a1, na, p1, tw1, tt1);
+    a_res = fft<T, SIGN, 0, Z0A>(a0, a1, na, p1, tw1, tt1);
     b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
 }
 
@@ -526,7 +549,7 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
+    C* res = fft<T, +1, ZF, (ZF == 0)>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
@@ -613,7 +636,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     }
     __syncthreads();
     C *r1, *r2;
-    fft_pair<T, +1, FUSE>(F1, F2, H1, H2, r1, r2, 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    fft_pair<T, +1, FUSE, true>(F1, F2, H1, H2, r1, r2, 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
     C* o1 = (r1 == F1) ? F2 : F1;              // free full buffer(s)
     C* o2 = (r2 == H1) ? H2 : H1;              // free half buffer
     C* p2 = (LAYOUT == 5) ? o1 + Mt : F3;      // where uw + i vw goes
