@@ -290,7 +290,7 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False)
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on
 # the paper workload 129 x 512 x 170, 32895 rows per launch; the per-row
 # traffic does not depend on Nr or Nz.
-ROWS_FP64_BYTES_PER_ROW = {512: (404993280 + 627219200) / 32895}
+ROWS_FP64_BYTES_PER_ROW = {512: (404830720 + 627351040) / 32895}
 
 
 def roofline_of(w, prec_name, ph, peaks):
