@@ -174,14 +174,20 @@ bool build_stencils(const std::vector<double>& r, HostStencils& S) {
 
 // Mixed-radix Stockham plans.  Family 0 (theta rows): radix-3 stages first,
 // then 4, then 2.  Family 1 (z columns): radix-3 stages, then 16, then one
-// stage of 8, 4 or 2.
+// stage of 8, 4 or 2.  Family 3 (float64 forward z): radix 4, then 2, then
+// the radix-3 stages last.
 bool make_plan(int M, FftPlan& p, std::vector<ld>& twre, std::vector<ld>& twim, int family) {
     p.M = M;
     p.nst = 0;
     int m = M, Ns = 1, off = 0;
     std::vector<int> radices;
+    if (family == 3) {                          // radix 4, 2, then 3 last
+        while (m % 4 == 0) { radices.push_back(4); m /= 4; }
+        while (m % 2 == 0) { radices.push_back(2); m /= 2; }
+    }
     while (m % 3 == 0) { radices.push_back(3); m /= 3; }
-    if (family == 0) {
+    if (family == 3) {
+    } else if (family == 0) {
         while (m % 4 == 0) { radices.push_back(4); m /= 4; }
         while (m % 2 == 0) { radices.push_back(2); m /= 2; }
     } else {
@@ -514,6 +520,15 @@ int init_handle(tc_handle* h) {
             std::vector<double> c = tangent_twiddles(d.pz0);
             if (!c.empty()) {
                 if ((rc_ = upload(h, d.twz_tan, c))) return rc_;
+                FftPlan p3;
+                std::vector<ld> r3, i3;
+                if (!make_plan(d.Mz, p3, r3, i3, 3) || p3.R[p3.nst - 1] != 3) {
+                    set_err("axial plan of family 3 does not end in a radix-3 stage");
+                    return TC_ERR_ARG;
+                }
+                std::vector<double> c3 = tangent_twiddles(p3);
+                if (c3.empty()) { set_err("axial plan of family 3 with a radix other than 2, 3, 4"); return TC_ERR_ARG; }
+                if ((rc_ = upload(h, d.twz3_tan, c3))) return rc_;
                 std::vector<float2> f0(r0.size() ? r0.size() : 1, make_float2(1.0f, 0.0f));
                 std::vector<float4> x0(r0.size() ? r0.size() : 1, make_float4(1.0f, 0.0f, 0.0f, 0.0f));
                 for (size_t i = 0; i < r0.size(); ++i) {
@@ -532,6 +547,15 @@ int init_handle(tc_handle* h) {
         if (a.empty() || b.empty()) { set_err("theta plan with a radix other than 2, 3, 4"); return TC_ERR_ARG; }
         if ((rc_ = upload(h, d.twt_tan, a))) return rc_;
         if ((rc_ = upload(h, d.twh_tan, b))) return rc_;
+        FftPlan p3;
+        std::vector<ld> r3, i3;
+        if (!make_plan(d.Mt, p3, r3, i3, 3) || p3.R[p3.nst - 1] != 3) {
+            set_err("theta plan of family 3 does not end in a radix-3 stage");
+            return TC_ERR_ARG;
+        }
+        std::vector<double> c3 = tangent_twiddles(p3);
+        if (c3.empty()) { set_err("theta plan of family 3 with a radix other than 2, 3, 4"); return TC_ERR_ARG; }
+        if ((rc_ = upload(h, d.twt3_tan, c3))) return rc_;
     }
     if ((rc_ = upload(h, d.twz_f, twz_f))) return rc_;
     if ((rc_ = upload(h, d.twt_f, twt_f))) return rc_;

@@ -168,9 +168,12 @@ __device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int n
 // multiply-adds and 16 adds; radix 3 takes 16 instead of 22.  Table layout
 // per jm as built on the host (tangent_twiddles).
 template <int R> __host__ __device__ constexpr int tan_entries() { return R == 2 ? 2 : 6; }
-template <int R, int SIGN>
+// With SKIP1 (radix 3 only) output r = 1 is not written: the last stage of a
+// transform whose middle band of outputs is never read.
+template <int R, int SIGN, bool SKIP1 = false>
 __device__ __forceinline__ void stockham_bfly_tan(const double2* sc, double2* dcol, int j, int nb, int Ns,
                                                   const double* __restrict__ tw) {
+    static_assert(!SKIP1 || R == 3, "only the radix-3 butterfly skips an output");
     const int jm = j % Ns;
     double2 v[R];
     #pragma unroll
@@ -193,7 +196,7 @@ __device__ __forceinline__ void stockham_bfly_tan(const double2* sc, double2* dc
         const double2 bm = make_double2(fma(-rho, u2.x, u1.x), fma(-rho, u2.y, u1.y));
         const double2 t0 = make_double2(fma(-hk, b.x, v[0].x), fma(-hk, b.y, v[0].y));
         dc[0] = make_double2(fma(k1, b.x, v[0].x), fma(k1, b.y, v[0].y));
-        dc[Ns] = make_double2(fma(sk, bm.y, t0.x), fma(-sk, bm.x, t0.y));
+        if constexpr (!SKIP1) dc[Ns] = make_double2(fma(sk, bm.y, t0.x), fma(-sk, bm.x, t0.y));
         dc[2 * Ns] = make_double2(fma(-sk, bm.y, t0.x), fma(sk, bm.x, t0.y));
     } else {
         const double2 u1 = tang(v[1], t[0]), u2 = tang(v[2], t[1]), u3 = tang(v[3], t[2]);
@@ -319,9 +322,18 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
 // the stage constants becomes a multiply-shift and the stage loop unrolls.
 // Family 0 (theta rows, few columns per block: many small butterflies):
 // radix-3 stages, then 4, then 2.  Family 1 (z columns, many columns per
-// block): radix-3 stages, then 16, then one stage of 8, 4 or 2.
+// block): radix-3 stages, then 16, then one stage of 8, 4 or 2.  Family 3
+// (float64 forward z transforms): radix 4, then 2, then the radix-3 stages
+// last, so that the last stage writes the outputs in three bands of M/3 and
+// a truncated transform can skip the middle band (see k_zfwd).
 __host__ __device__ constexpr int plan_radix_f(int M, int s, int F) {
     int i = 0;
+    if (F == 3) {
+        while (M % 4 == 0) { if (i == s) return 4; M /= 4; ++i; }
+        while (M % 2 == 0) { if (i == s) return 2; M /= 2; ++i; }
+        while (M % 3 == 0) { if (i == s) return 3; M /= 3; ++i; }
+        return 1;
+    }
     while (M % 3 == 0) { if (i == s) return 3; M /= 3; ++i; }
     if (F == 0) {
         while (M % 4 == 0) { if (i == s) return 4; M /= 4; ++i; }
@@ -347,9 +359,9 @@ __host__ __device__ constexpr int plan_off_f(int M, int s, int F) {
     return o;
 }
 
-__host__ __device__ constexpr int plan_tan_off(int M, int s) {
+__host__ __device__ constexpr int plan_tan_off(int M, int s, int F = 0) {
     int o = 0;
-    for (int i = 0; i < s; ++i) o += plan_ns_f(M, i, 0) * (plan_radix_f(M, i, 0) == 2 ? 2 : 6);
+    for (int i = 0; i < s; ++i) o += plan_ns_f(M, i, F) * (plan_radix_f(M, i, F) == 2 ? 2 : 6);
     return o;
 }
 
@@ -375,6 +387,7 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
                                                               int ncols, const typename V2<T>::t* __restrict__ tw,
                                                               const double* __restrict__ twtan) {
     typedef typename V2<T>::t C;
+    static_assert(F != 3 || std::is_same<T, double>::value, "family 3 has float64 tangent twiddles only");
     if constexpr (S == plan_nst_f(M, F)) {
         return src;
     } else {
@@ -387,8 +400,10 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
             const int j = b - col * nb;
             if constexpr (Z0 && S == 0 && R == 3)
                 stockham_bfly3_zero_mid<SIGN, T>(src + col * M, dst + col * M, j, nb);
-            else if constexpr (std::is_same<T, double>::value && F == 0 && Ns > 1)
-                stockham_bfly_tan<R, SIGN>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S));
+            else if constexpr (F == 3 && S + 1 == plan_nst_f(M, F))   // last stage, radix 3: skip band 1
+                stockham_bfly_tan<R, SIGN, true>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S, F));
+            else if constexpr (std::is_same<T, double>::value && (F == 0 || F == 3) && Ns > 1)
+                stockham_bfly_tan<R, SIGN>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S, F));
             else
                 stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
         }
@@ -402,7 +417,9 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
 // the supported grids (those of tc_fft_fixed_length), the run-time plan
 // otherwise (same arithmetic).
 // Z0: the input is a 3/2-padded spectrum (middle third zero), which the
-// first stage of the compile-time plans skips.
+// first stage of the compile-time plans skips.  Families 0 and 3 of the
+// float64 z transforms are launched only for lengths with a compile-time
+// plan (the host checks tc_fft_fixed_length).
 template <typename T, int SIGN, int F, bool Z0 = false>
 __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw,
@@ -415,7 +432,7 @@ __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* bu
             TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
             TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
             TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
-            default: return fft_stockham<T, SIGN, F>(buf0, buf1, ncols, pl, tw);
+            default: return fft_stockham<T, SIGN, (F == 3 ? 0 : F)>(buf0, buf1, ncols, pl, tw);
         }
     }
 #undef TC_FFT_CASE
@@ -425,59 +442,67 @@ __device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* bu
 // half length M2) advanced stage by stage in one loop, one barrier per
 // stage for both; each keeps its own plan, twiddles and ping-pong pair.  On
 // return a_res / b_res hold the buffers with the results.
-template <typename T, int SIGN, int M, int S, bool Z0 = false>
+// F: plan family of this transform (0, or 3 for a float64 full-length
+// forward transform whose middle band of outputs is not read).
+template <typename T, int SIGN, int M, int S, bool Z0 = false, int F = 0>
 __device__ __forceinline__ void pair_bfly(typename V2<T>::t* src, typename V2<T>::t* dst, int j,
                                           const typename V2<T>::t* __restrict__ tw,
                                           const double* __restrict__ twtan) {
-    constexpr int R = plan_radix_f(M, S, 0);
-    constexpr int Ns = plan_ns_f(M, S, 0);
+    static_assert(F == 0 || (F == 3 && std::is_same<T, double>::value), "family 3 is float64 only");
+    constexpr int R = plan_radix_f(M, S, F);
+    constexpr int Ns = plan_ns_f(M, S, F);
     constexpr int nb = M / R;
     if constexpr (Z0 && S == 0 && R == 3)
         stockham_bfly3_zero_mid<SIGN, T>(src, dst, j, nb);
+    else if constexpr (F == 3 && S + 1 == plan_nst_f(M, F))   // last stage, radix 3: skip band 1
+        stockham_bfly_tan<R, SIGN, true>(src, dst, j, nb, Ns, twtan + plan_tan_off(M, S, F));
     else if constexpr (std::is_same<T, double>::value && Ns > 1)
-        stockham_bfly_tan<R, SIGN>(src, dst, j, nb, Ns, twtan + plan_tan_off(M, S));
+        stockham_bfly_tan<R, SIGN>(src, dst, j, nb, Ns, twtan + plan_tan_off(M, S, F));
     else
-        stockham_bfly<R, SIGN, T>(src, dst, j, nb, Ns, tw + plan_off_f(M, S, 0));
+        stockham_bfly<R, SIGN, T>(src, dst, j, nb, Ns, tw + plan_off_f(M, S, F));
 }
-template <typename T, int SIGN, int M1, int M2, int S, bool Z0A = false>
+template <typename T, int SIGN, int M1, int M2, int S, bool Z0A = false, int FA = 0>
 __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V2<T>::t* a1,
                                                typename V2<T>::t* b0, typename V2<T>::t* b1,
                                                typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                                                const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
                                                const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
-    constexpr int n1 = plan_nst_f(M1, 0), n2 = plan_nst_f(M2, 0);
+    constexpr int n1 = plan_nst_f(M1, FA), n2 = plan_nst_f(M2, 0);
     if constexpr (S >= n1 && S >= n2) {
         a_res = a0;
         b_res = b0;
     } else {
         constexpr bool A = S < n1, B = S < n2;
-        constexpr int nb1 = A ? M1 / plan_radix_f(M1, S, 0) : 0;
+        constexpr int nb1 = A ? M1 / plan_radix_f(M1, S, FA) : 0;
         constexpr int nb2 = B ? M2 / plan_radix_f(M2, S, 0) : 0;
         const int nA = A ? na * nb1 : 0;
         for (int b = threadIdx.x; b < nA + nb2; b += blockDim.x) {
             if constexpr (A) {
                 if (b < nA) {
                     const int col = b / nb1;
-                    pair_bfly<T, SIGN, M1, (A ? S : 0), Z0A>(a0 + col * M1, a1 + col * M1, b - col * nb1, tw1, tt1);
+                    pair_bfly<T, SIGN, M1, (A ? S : 0), Z0A, FA>(a0 + col * M1, a1 + col * M1, b - col * nb1, tw1, tt1);
                     continue;
                 }
             }
             if constexpr (B) pair_bfly<T, SIGN, M2, (B ? S : 0)>(b0, b1, b - nA, tw2, tt2);
         }
         __syncthreads();
-        fft_pair_stage<T, SIGN, M1, M2, S + 1, Z0A>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
-                                                    a_res, b_res, na, tw1, tt1, tw2, tt2);
+        fft_pair_stage<T, SIGN, M1, M2, S + 1, Z0A, FA>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
+                                                        a_res, b_res, na, tw1, tt1, tw2, tt2);
     }
 }
 // Full-length (plan p1, na contiguous columns) and half-length (plan p2,
 // one column) transforms together when FUSE is set and both lengths have
-// compile-time plans, else one after the other.
-template <typename T, int SIGN, bool FUSE, bool Z0A = false>
+// compile-time plans, else one after the other.  FA: plan family of the
+// full-length transform (tt1 then holds that family's tangent twiddles;
+// p1 and tw1 stay the family-0 plan, used only where a length has no
+// compile-time plan).
+template <typename T, int SIGN, bool FUSE, bool Z0A = false, int FA = 0>
 __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename V2<T>::t* b0, typename V2<T>::t* b1,
                          typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                          const FftPlan& p1, const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
                          const FftPlan& p2, const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
-#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0, Z0A>(a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
+#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0, Z0A, FA>(a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
     if constexpr (FUSE) {
         switch (p1.M) {
             TC_PAIR_CASE(24) TC_PAIR_CASE(36) TC_PAIR_CASE(48) TC_PAIR_CASE(72) TC_PAIR_CASE(96)
@@ -487,7 +512,7 @@ __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename 
         }
     }
 #undef TC_PAIR_CASE
-    a_res = fft<T, SIGN, 0, Z0A>(a0, a1, na, p1, tw1, tt1);
+    a_res = fft<T, SIGN, FA, Z0A>(a0, a1, na, p1, tw1, tt1);
     b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
 }
 
@@ -640,33 +665,59 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     C* o1 = (r1 == F1) ? F2 : F1;              // free full buffer(s)
     C* o2 = (r2 == H1) ? H2 : H1;              // free half buffer
     C* p2 = (LAYOUT == 5) ? o1 + Mt : F3;      // where uw + i vw goes
+    // Float64: the forward factor 1/(Mt Mz) and the 1/2 of the real-pair
+    // unpacking below are applied here, as s = 1/(2 Mt Mz) on one factor of
+    // every product (three multiplies per point), instead of two multiplies
+    // per output value in the unpacking and two more in k_zfwd.
+    constexpr bool PRE = std::is_same<T, double>::value;
+    const T s = PRE ? (T)(0.5 * d.fscale) : (T)1;
     for (int m = threadIdx.x; m < H; m += blockDim.x) {
         const C w2 = r2[m];
         T bb[2];
         for (int e = 0; e < 2; ++e) {
             const int p = 2 * m + e;
             const T u = r1[p].x, v = r1[p].y, w = e ? w2.y : w2.x;
-            const T vv = v * v;
             C b0, b1;
-            b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
-            b1.x = u * w; b1.y = v * w;          // uw, vw
+            if constexpr (PRE) {
+                const T us = s * u, vs = s * v, ws = s * w;
+                const T vv = vs * v;
+                b0.x = us * u - vv; b0.y = us * v;   // s (uu - vv), s uv
+                b1.x = us * w; b1.y = vs * w;        // s uw, s vw
+                bb[e] = ws * w - vv;                 // s (ww - vv)
+            } else {
+                const T vv = v * v;
+                b0.x = u * u - vv; b0.y = u * v;     // uu - vv, uv
+                b1.x = u * w; b1.y = v * w;          // uw, vw
+                bb[e] = w * w - vv;                  // ww - vv
+            }
             o1[p] = b0; p2[p] = b1;
-            bb[e] = w * w - vv;                  // ww - vv
         }
         C z; z.x = bb[0]; z.y = bb[1];
         o2[m] = z;
     }
     __syncthreads();
+    // float64 forward full-length transforms in plan family 3: the unpacking
+    // below reads outputs j < Nh and Mt - j only, never the band Nh .. 2 Nh - 1
+    constexpr int FA = PRE ? 3 : 0;
+    const double* tta = PRE ? d.twt3_tan : d.twt_tan;
     C *s1, *s3;
-    fft_pair<T, -1, FUSE>(o1, r1, o2, r2, s1, s3, LAYOUT == 5 ? 2 : 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    fft_pair<T, -1, FUSE, false, FA>(o1, r1, o2, r2, s1, s3, LAYOUT == 5 ? 2 : 1, d.pt, twt<T>(d), tta, d.ph, twh<T>(d), d.twh_tan);
     C* pb = reinterpret_cast<C*>(d.pbuf);
     // unpack two real transforms from one complex transform of length Mt
+    auto half = [](T x) -> T {                 // the unpacking's 1/2 (already in s for float64)
+        if constexpr (PRE) return x;
+        else return (T)0.5 * x;
+    };
+    auto mhalf = [](T x) -> T {
+        if constexpr (PRE) return -x;
+        else return (T)-0.5 * x;
+    };
     auto unpack_full = [&](const C* out, int j, int slot) {
         const C cj = out[j];
         const C cm = out[j == 0 ? 0 : Mt - j];
         C x1, x2;
-        x1.x = (T)0.5 * (cj.x + cm.x); x1.y = (T)0.5 * (cj.y - cm.y);
-        x2.x = (T)0.5 * (cj.y + cm.y); x2.y = (T)-0.5 * (cj.x - cm.x);
+        x1.x = half(cj.x + cm.x); x1.y = half(cj.y - cm.y);
+        x2.x = half(cj.y + cm.y); x2.y = mhalf(cj.x - cm.x);
         pb[(((size_t)slot * Nr + r) * Mz + q) * Nh + j] = x1;
         pb[(((size_t)(slot + 1) * Nr + r) * Mz + q) * Nh + j] = x2;
     };
@@ -679,9 +730,9 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
             const C zk = s3[j];
             const C zm = s3[j == 0 ? 0 : H - j];
             C ev, od, x;
-            ev.x = (T)0.5 * (zk.x + zm.x); ev.y = (T)0.5 * (zk.y - zm.y);
+            ev.x = half(zk.x + zm.x); ev.y = half(zk.y - zm.y);
             // (Z_k - conj Z_{H-k})/(2i)
-            od.x = (T)0.5 * (zk.y + zm.y); od.y = (T)-0.5 * (zk.x - zm.x);
+            od.x = half(zk.y + zm.y); od.y = mhalf(zk.x - zm.x);
             const C t = tr[j];
             x.x = ev.x + od.x * t.x - od.y * t.y;
             x.y = ev.y + od.x * t.y + od.y * t.x;
@@ -690,12 +741,12 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     }
     if constexpr (LAYOUT == 4) {
         // uw + i vw: its ping-pong partner is the full buffer not holding s1
-        C* s2 = fft<T, -1, 0>(F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), d.twt_tan);
+        C* s2 = fft<T, -1, FA>(F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), tta);
         for (int j = threadIdx.x; j < Nh; j += blockDim.x) unpack_full(s2, j, 2);   // uw, vw
     }
 }
 
-// ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) -----------------
+// ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) (float64: already in pbuf) ----
 template <typename T, int ZF>
 __global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
     typedef typename V2<T>::t C;
@@ -713,9 +764,12 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
-    C* res = fft<T, -1, ZF>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
+    // family 3 (float64): the last stage skips outputs M/3 .. 2M/3 - 1, i.e.
+    // q = Nz/2 .. Nz - 1, which the truncation below never reads
+    C* res = fft<T, -1, ZF>(buf0, buf1, ct, (ZF == 0 || ZF == 3) ? d.pz0 : d.pz, twz_of<T, ZF>(d),
+                            ZF == 3 ? d.twz3_tan : d.twz_tan);
     T scale;
-    if constexpr (std::is_same<T, double>::value) scale = d.fscale;
+    if constexpr (std::is_same<T, double>::value) scale = 1.0;     // applied in k_rows
     else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;
     else scale = dfloat(d.fscale_f, d.fscale_lo);
     // products: double2 for float64, float2 for the mixed form, double-float
@@ -729,7 +783,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
             const int n = s < Nz / 2 ? s : s - Nz;
             const int qq = n >= 0 ? n : Mz + n;
             val = res[c * Mz + qq];
-            val.x *= scale; val.y *= scale;
+            if constexpr (!std::is_same<T, double>::value) { val.x *= scale; val.y *= scale; }
         }
         outp[(size_t)s * Nh + j0 + c] = val;
     }
@@ -775,8 +829,10 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
     } else {
         const dim3 g(ntiles, d.Nr, TC_NPROD);
         if (odd) k_zfwd<T, 2><<<g, 256, smz, s>>>(d, tile0);
-        else if (fam0) k_zfwd<T, 0><<<g, 256, smz, s>>>(d, tile0);
-        else k_zfwd<T, 1><<<g, 256, smz, s>>>(d, tile0);
+        else if (fam0) {
+            if constexpr (std::is_same<T, double>::value) k_zfwd<T, 3><<<g, 256, smz, s>>>(d, tile0);
+            else k_zfwd<T, 0><<<g, 256, smz, s>>>(d, tile0);
+        } else k_zfwd<T, 1><<<g, 256, smz, s>>>(d, tile0);
     }
 }
 
@@ -793,6 +849,7 @@ static cudaError_t plane_attributes_t() {
     constexpr bool fuse = !std::is_same<T, dfloat>::value;
     set((const void*)k_zinv<T, 0>); set((const void*)k_zinv<T, 1>); set((const void*)k_zinv<T, 2>);
     set((const void*)k_zfwd<T, 0>); set((const void*)k_zfwd<T, 1>); set((const void*)k_zfwd<T, 2>);
+    if constexpr (std::is_same<T, double>::value) set((const void*)k_zfwd<T, 3>);
     set((const void*)k_rows<T, 5, fuse>); set((const void*)k_rows<T, 4, fuse>);
     return e;
 }

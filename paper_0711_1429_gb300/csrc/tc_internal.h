@@ -87,6 +87,8 @@ struct TcDev {
     int zfam0;
     FftPlan pz0;
     const double* twz_tan;
+    const double* twz3_tan;     // tangent twiddles of the family-3 plan (float64 forward z)
+    const double* twt3_tan;     // tangent twiddles of the family-3 plan of Mt (float64 forward theta)
     // twiddles of the plan pz0 in the plain (cos, sin) form for the float32
     // and double-float z transforms, which use that plan too
     const float2* twz0_f;
