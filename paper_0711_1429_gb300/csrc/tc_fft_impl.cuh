@@ -516,8 +516,9 @@ __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename 
     b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
 }
 
-// z twiddles of the plan the kernel runs: pz (family 1) or pz0 (family 0;
-// float64 reads the tangent table instead and never this one)
+// z twiddles of the plan the kernel runs: pz (family 1) or pz0 (family 0).
+// Float64 kernels of families 0 and 3 read their tangent tables (twz_tan,
+// twz3_tan) instead, and never the table returned here.
 template <typename T, int ZF> __device__ __forceinline__ const typename V2<T>::t* twz_of(const TcDev& d);
 template <typename T> __device__ __forceinline__ const typename V2<T>::t* twz(const TcDev& d);
 template <> __device__ __forceinline__ const dcomplex* twz<dfloat>(const TcDev& d) { return reinterpret_cast<const dcomplex*>(d.twz_x); }
