@@ -157,6 +157,9 @@ def _check(rc):
 
 
 def tc_create(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt):
+    """New FP64 case on the current device: Nr radial points, Ntheta x Nz
+    Fourier modes, radius ratio R_i/R_o, Reynolds numbers of the inner and
+    outer cylinder on the gap, time step in h/W_i.  Laminar Couette start."""
     h = lib().tc_create(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt)
     if not h:
         raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
@@ -171,6 +174,9 @@ def make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0,
 
 def tc_create_ex(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0, Lz=0.0,
                  precision=TC_PREC_FP64, device=-1, autotune=0, stretch=0.0):
+    """New case with the full parameter set: box (Theta in radians, Lz in h;
+    0 for the default box), arithmetic form (TC_PREC_*), device, tile autotuning and
+    tanh stretching of the radial grid."""
     p = make_params(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta, Lz, precision, device,
                     autotune, stretch)
     h = lib().tc_create_ex(ctypes.byref(p))
@@ -180,10 +186,13 @@ def tc_create_ex(Nr, Ntheta, Nz, radius_ratio, Re_inner, Re_outer, dt, Theta=0.0
 
 
 def tc_step(h, nsteps=1):
+    """Advance by `nsteps` full three-substep Runge-Kutta steps; raises
+    TcError (e.g. TC_ERR_NONFINITE) on failure."""
     return _check(lib().tc_step(h, nsteps))
 
 
 def tc_advance_substeps(h, nsub=1):
+    """Advance by `nsub` single Runge-Kutta substeps (phase kept across calls)."""
     return _check(lib().tc_advance_substeps(h, nsub))
 
 
@@ -213,6 +222,8 @@ def tc_get_field(h, which, space=TC_SPECTRAL, out=None):
 
 
 def tc_set_field(h, which, arr):
+    """Set v or eta (complex128 [Nr][Nz][Ntheta/2]) or the mean profile U or
+    W (float64 [Nr]); setting v or eta restarts the Runge-Kutta memory."""
     arr = np.ascontiguousarray(arr)
     if which in (TC_FIELD_MEAN_U, TC_FIELD_MEAN_W):
         arr = np.ascontiguousarray(arr, dtype=np.float64)
@@ -231,12 +242,17 @@ def tc_get_field_ptr(h, which, space, host_ptr, nbytes):
 
 
 def tc_torque_stats(h):
+    """Diagnostics of the current state as a dict: time, step, inner and
+    outer torque, Re_tau at both walls, kinetic energy, dissipation and wall
+    power."""
     s = tc_stats()
     _check(lib().tc_torque_stats(h, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in tc_stats._fields_}
 
 
 def tc_set_stream(h, stream_ptr):
+    """Launch this case's work on the given CUDA stream (a cudaStream_t as
+    an integer, e.g. torch.cuda.Stream().cuda_stream)."""
     return _check(lib().tc_set_stream(h, stream_ptr))
 
 
@@ -249,6 +265,8 @@ def tc_save_state(h):
 
 
 def tc_load_state(h, image):
+    """Restore a state image from tc_save_state of a case of the same shape;
+    the next step continues bit for bit."""
     buf = ctypes.create_string_buffer(image, len(image))
     return _check(lib().tc_load_state(h, buf, len(image)))
 
@@ -257,6 +275,9 @@ LINE_VARIANTS = (64, 128, 256, 1003, 1004, 2007)
 
 
 def tc_set_tiles(h, ztile=0, line_variant=0, chunks=0):
+    """Pin the z tile, the line-kernel variant (LINE_VARIANTS) and the column
+    groups of the overlapped step; 0 keeps the current choice.  No launch
+    shape changes the results."""
     return _check(lib().tc_set_tiles(h, ztile, line_variant, chunks))
 
 
@@ -277,6 +298,7 @@ def tc_device_bytes(h):
 
 
 def tc_destroy(h):
+    """Free the case and all of its device memory (None is ignored)."""
     if h:
         lib().tc_destroy(h)
 
