@@ -22,7 +22,9 @@ What it computes, and where each piece comes from in the paper:
                    conditions v = Dv = eta = 0 (Appendix).
 * rk.py         -- the 3-substep IMEX Runge-Kutta step (Sec. 2.1, Sec. 3.1).
 * diagnostics.py-- torque, Eq. 2 (reading fixed by Table 2), Re_tau (Sec. 5),
-                   kinetic energy.
+                   kinetic energy, and the energy budget the paper does not
+                   print: viscous dissipation nu <2 S:S> and the power of the
+                   wall shear (dE/dt = P_in - eps).
 * linear.py     -- linearised operator of one Fourier mode about circular
                    Couette flow, used to pin the critical Reynolds numbers of
                    Sec. 3.
