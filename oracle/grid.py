@@ -10,7 +10,7 @@ Paper references (Pirro & Quadrio):
   * Appendix: Fourier expansion in theta and z with wavenumbers m (azimuthal)
     and alpha (axial); k^2 = alpha^2 + m^2/r^2.
 
-Mode layout (shared convention, stated in the design notes): azimuthal index
+Mode layout (the convention of the library's C header as well): azimuthal index
 j = 0..Ntheta/2-1 with m_j = j*m0 (the half spectrum; the theta Nyquist is
 dropped), axial slots in FFT order n = 0..Nz/2-1, [Nz/2 = Nyquist, always 0],
 -Nz/2+1..-1 with alpha_n = n*alpha0.  Spectral arrays are shaped

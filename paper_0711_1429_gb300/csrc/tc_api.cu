@@ -78,11 +78,13 @@ ld hop(int which, int q, ld x, ld xc, ld h) {
 
 
 
-// Stencils of the 5-point compact explicit scheme (see the oracle's notes on
-// the reading): interior rows make D D_* D D_* exact to degree 8 jointly with
-// d0 (sum d0 = 1), then D D_* and D exact to degree 4 against that d0;
-// near-wall rows 1, Nr-2 explicit one-sided to degree 4; wall derivative
-// rows for the Neumann condition and the wall shear.
+// Stencils of the 5-point compact explicit scheme (Sec. 2.1: five points,
+// order at least 4, coefficients by polynomial matching; the paper leaves the
+// construction open, and this is the reading used): interior rows make
+// D D_* D D_* exact to degree 8 jointly with d0 (sum d0 = 1), then D D_* and
+// D exact to degree 4 against that d0; near-wall rows 1, Nr-2 explicit
+// one-sided to degree 4; wall derivative rows for the Neumann condition and
+// the wall shear.
 bool build_stencils(const std::vector<double>& r, HostStencils& S) {
     const int N = (int)r.size();
     S.start.assign(N, 0);
