@@ -1,12 +1,12 @@
-"""The GPU hot path reproduces the critical Reynolds number of Sec. 3.
+"""The GPU hot path reproduces the critical Reynolds numbers of Sec. 3.
 
 A Taylor-vortex mode (m = 0, alpha = 2 pi/4, the straight-vortex box of
-Table 1) of amplitude 1e-6 is time-marched through tc_step at zeta = 0.5
-just below and just above the paper's bracket 68.2 < Re_c < 68.4.  After
-the transients decay, the growth rate of |v_hat| must change sign across the
-bracket and agree with the leading eigenvalue of the oracle's linearised
-rows (same discretisation, no time-stepping error worth the name at this
-dt).
+Table 1) of amplitude 1e-6 is time-marched through tc_step just below and
+just above the paper's brackets: 68.2 < Re_c < 68.4 at zeta = 0.5 and
+184 < Re_c < 186 at zeta = 0.95.  After the transients decay, the growth
+rate of |v_hat| must change sign across the bracket and agree with the
+leading eigenvalue of the oracle's linearised rows (same discretisation, no
+time-stepping error worth the name at this dt).
 """
 import math
 
@@ -23,9 +23,9 @@ from helpers import ensure_lib
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_rate(Re, Nr=33, dt=0.05, t1=40.0, t2=80.0):
+def _gpu_rate(Re, Nr=33, dt=0.05, t1=40.0, t2=80.0, zeta=0.5):
     ensure_lib()
-    h = tc.tc_create_ex(Nr, 4, 4, 0.5, Re, 0.0, dt, Lz=4.0)
+    h = tc.tc_create_ex(Nr, 4, 4, zeta, Re, 0.0, dt, Lz=4.0)
     try:
         Nz, Nh = 4, 2
         x = -1.0 + 2.0 * np.arange(Nr) / (Nr - 1)
@@ -52,3 +52,17 @@ def test_critical_reynolds_bracket_on_gpu():
         rates[Re] = (g, e)
         assert abs(g - e) < 2e-4, (Re, g, e)
     assert rates[68.0][0] < 0 < rates[68.6][0], rates
+
+
+def test_critical_reynolds_bracket_on_gpu_zeta_095():
+    """zeta = 0.95 (R_i = 38 h): the growth rates at 184 and 186 are only
+    -/+ 3.8e-4, and the next eigenvalue lies 0.12 below; the rate is taken
+    between t = 100 and 200, where the second mode has decayed by e^-12."""
+    S = build_stencils(Case(33, 4, 4, 0.95, 185.0, 0.0, 0.05).r)
+    rates = {}
+    for Re in (184.0, 186.0):
+        g = _gpu_rate(Re, t1=100.0, t2=200.0, zeta=0.95)
+        e = growth_rate(Case(33, 4, 4, 0.95, Re, 0.0, 0.05, Lz=4.0), S, 0.0, 2 * math.pi / 4.0)
+        rates[Re] = (g, e)
+        assert abs(g - e) < 5e-5, (Re, g, e)
+    assert rates[184.0][0] < 0 < rates[186.0][0], rates
