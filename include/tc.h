@@ -297,10 +297,15 @@ void tc_server_destroy(tc_server* s);
  * work is queued on cuda_stream (NULL: legacy default stream) and the call
  * returns without waiting.
  *
- * Its one intermediate (a (3Nz/2) x (Ntheta/2) complex plane) and the
- * twiddle tables live in a static device array of TC_NOALLOC_SCRATCH_BYTES
- * that every GPU loading the library holds until the process exits.  Sizes
- * whose plane and tables exceed it are rejected with TC_ERR_SIZE.  The first
+ * Its intermediates (the z-transformed (3Nz/2) x (Ntheta/2) complex planes,
+ * as many radial planes per pass as fit) and the twiddle tables, computed on
+ * the device at every call, live in a static device array of
+ * TC_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Sizes for which one plane plus the tables exceeds it, or
+ * whose padded lengths need more than 200 KB of shared memory per transform
+ * block (2 x 16 bytes per point of 3Nz/2 or 3Ntheta/2, times the 1-8 columns
+ * of a z block), are rejected with TC_ERR_SIZE before anything is queued.
+ * The first
  * call on a device does a one-time set-up with that device current (it
  * fetches the array's device address and opts the kernels into large shared
  * memory); make that first call before any stream capture.  All calls share

@@ -19,6 +19,7 @@ TC_OK, TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_NONFINITE, TC_ERR_SIZE, TC_ERR_TIMEOUT, T
 TC_FIELD_U, TC_FIELD_V, TC_FIELD_W, TC_FIELD_ETA, TC_FIELD_MEAN_U, TC_FIELD_MEAN_W = range(6)
 TC_SPECTRAL, TC_PHYSICAL = 0, 1
 TC_PREC_FP64, TC_PREC_MIXED, TC_PREC_DF64 = 0, 1, 2
+TC_NOALLOC_SCRATCH_BYTES = 16 << 20     # size of the fixed array of tc_to_physical_noalloc
 
 
 class TcError(RuntimeError):

@@ -20,6 +20,22 @@ struct FftPlan {
     int ntw;
 };
 
+// Entry i of stage s of the twiddle table of plan p as the fraction num/den
+// of a full turn: the entry is exp(-2 pi i num/den).  Entries i < Ns (R-1)
+// are the stage twiddles (jm = i / (R-1), r = i % (R-1) + 1: num = r jm,
+// den = Ns R); a stage of odd prime radix R > 3 stores its R-th roots
+// (num = e, den = R) after them.  Returns the number of entries of the stage
+// (i is ignored when it is out of range).
+__host__ __device__ inline int fft_twiddle_fraction(const FftPlan& p, int s, int i, long long& num, long long& den) {
+    const int R = p.R[s], Ns = p.Ns[s];
+    const bool roots = !(R == 2 || R == 3 || R == 4 || R == 8 || R == 16);
+    const int nstage = Ns * (R - 1);
+    if (i < nstage) { num = (long long)(i % (R - 1) + 1) * (i / (R - 1)); den = (long long)Ns * R; }
+    else { num = i - nstage; den = R; }
+    num %= den;
+    return nstage + (roots ? R : 0);
+}
+
 // Everything a kernel needs, passed by value.
 struct TcDev {
     int Nr, Nz, Nh, Mt, Mz;

@@ -6,16 +6,24 @@
 // starts, plug-ins whose host application owns every device buffer, or
 // latency-critical loops in which cudaMalloc (which may synchronise the
 // device) is forbidden.  tc_to_physical_noalloc serves them: the caller
-// passes the input and output device buffers, and the one intermediate the
-// transform needs (the z-transformed plane, plus the twiddle tables) lives in
+// passes the input and output device buffers, and the intermediates the
+// transform needs (the z-transformed planes and the twiddle tables) live in
 // the fixed array below, which is part of the library image.
 //
 // The array is a host-side stand-in in host code: its device address is
 // fetched with cudaGetSymbolAddress once per device, with that device
 // current, the first time the entry point runs there.
+//
+// Nothing crosses from host memory during a call: the twiddle tables are
+// computed on the device from the transform plans (cached on the host per
+// pair of lengths), and as many radial planes as the array holds go through
+// each pair of launches.
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "tc_internal.h"
@@ -29,8 +37,12 @@ void tc_set_error_message(const std::string& s);
 namespace {
 
 const int kMaxDevices = 64;
+// shared memory the transform kernels may opt into (the library's own limit)
+const size_t kSmemLimit = 200 * 1024;
 unsigned char* g_scratch_dev[kMaxDevices];
 std::mutex g_setup_mutex;
+std::mutex g_plan_mutex;
+std::map<std::pair<int, int>, std::pair<FftPlan, FftPlan>> g_plans;   // (Mz, Mt) -> (z plan, theta plan)
 
 bool is_2a3b(int n) {
     if (n < 1) return false;
@@ -47,6 +59,24 @@ bool is_smooth(int n) {
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The z plan (radix 3, 16, then 8/4/2, plus the paired prime stages) and the
+// theta plan (radix 3, 4, 2) of the transform, built once per pair of lengths.
+bool plans_for(int Mz, int Mt, FftPlan& pz, FftPlan& pt) {
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    auto it = g_plans.find({Mz, Mt});
+    if (it == g_plans.end()) {
+        FftPlan a, b;
+        std::vector<long double> re, im;
+        if (!tc_build_fft_plan(Mz, a, re, im, 1)) return false;
+        re.clear(); im.clear();
+        if (!tc_build_fft_plan(Mt, b, re, im, 0)) return false;
+        it = g_plans.emplace(std::make_pair(Mz, Mt), std::make_pair(a, b)).first;
+    }
+    pz = it->second.first;
+    pt = it->second.second;
+    return true;
+}
 
 // Device address of the scratch array for the current device (set-up on the
 // first call per device: symbol address and the shared-memory opt-in of the
@@ -79,6 +109,25 @@ int scratch_for_current_device(unsigned char** out) {
 
 }  // namespace
 
+// Twiddle table of one plan, in the layout the transform kernels read
+// (FftPlan): per stage s of radix R after Ns points, exp(-2 pi i r jm/(Ns R))
+// for jm < Ns, r = 1..R-1, and for a stage of odd prime radix R the R-th roots
+// exp(-2 pi i e/R), e < R, after them (fft_twiddle_fraction).  One block per
+// stage; the angle is an exact fraction of a turn, reduced below one turn,
+// before sincospi.
+__global__ void k_noalloc_twiddles(FftPlan p, double2* tw) {
+    const int s = blockIdx.x;
+    if (s >= p.nst) return;
+    long long num, den;
+    const int count = fft_twiddle_fraction(p, s, 0, num, den);
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        fft_twiddle_fraction(p, s, i, num, den);
+        double sn, cs;
+        sincospi(2.0 * (double)num / (double)den, &sn, &cs);
+        tw[p.twoff[s] + i] = make_double2(cs, -sn);
+    }
+}
+
 extern "C" int tc_to_physical_noalloc(int Nr, int Ntheta, int Nz, const void* spectral_dev,
                                       void* physical_dev, void* cuda_stream) {
     if (Nr < 1 || Ntheta < 4 || Nz < 4 || Ntheta % 4 || Nz % 2 || !is_2a3b(Ntheta) || !is_smooth(Nz)) {
@@ -92,28 +141,34 @@ extern "C" int tc_to_physical_noalloc(int Nr, int Ntheta, int Nz, const void* sp
     }
     TcDev d;
     memset(&d, 0, sizeof(d));
-    d.Nr = 1;
     d.Nz = Nz;
     d.Nh = Ntheta / 2;
     d.Mt = 3 * Ntheta / 2;
     d.Mz = 3 * Nz / 2;
     d.npairs = d.Nz * d.Nh;
-    d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
-    std::vector<long double> zr, zi, tr, ti;
-    if (!tc_build_fft_plan(d.Mz, d.pz, zr, zi, 1) || !tc_build_fft_plan(d.Mt, d.pt, tr, ti, 0)) {
-        tc_set_error_message("tc_to_physical_noalloc: FFT length is not of the form 2^a 3^b");
+    // Shared memory per block: 2 ztile Mz complex values in the z transform,
+    // 2 Mt in the theta transform.  The z tile is the widest of 8, 4, 2, 1
+    // columns that divides Ntheta/2 and fits.
+    d.ztile = 0;
+    for (int t : {8, 4, 2, 1})
+        if (d.Nh % t == 0 && 2 * (size_t)t * d.Mz * sizeof(double2) <= kSmemLimit) { d.ztile = t; break; }
+    if (d.ztile == 0 || 2 * (size_t)d.Mt * sizeof(double2) > kSmemLimit) {
+        tc_set_error_message("tc_to_physical_noalloc: a padded transform length (3 Nz/2 = " + std::to_string(d.Mz) +
+                             ", 3 Ntheta/2 = " + std::to_string(d.Mt) + ") needs more than the " +
+                             std::to_string(kSmemLimit) + " bytes of shared memory a transform block may use");
+        return TC_ERR_SIZE;
+    }
+    if (!plans_for(d.Mz, d.Mt, d.pz, d.pt)) {
+        tc_set_error_message("tc_to_physical_noalloc: no transform plan for the padded lengths 3 Nz/2 = " +
+                             std::to_string(d.Mz) + " and 3 Ntheta/2 = " + std::to_string(d.Mt) +
+                             " (at most 16 stages of radix 2, 3, 4, 8, 16 and primes up to 17)");
         return TC_ERR_ARG;
     }
-    std::vector<double2> tw(zr.size() + tr.size() + 2);
-    size_t nz = zr.size() ? zr.size() : 1, nt = tr.size() ? tr.size() : 1;
-    for (size_t i = 0; i < zr.size(); ++i) tw[i] = make_double2((double)zr[i], (double)zi[i]);
-    if (zr.empty()) tw[0] = make_double2(1.0, 0.0);
-    for (size_t i = 0; i < tr.size(); ++i) tw[nz + i] = make_double2((double)tr[i], (double)ti[i]);
-    if (tr.empty()) tw[nz] = make_double2(1.0, 0.0);
+    const size_t nz = d.pz.ntw ? d.pz.ntw : 1, nt = d.pt.ntw ? d.pt.ntw : 1;
     const size_t tw_bytes = align256((nz + nt) * sizeof(double2));
     const size_t plane_bytes = (size_t)d.Mz * d.Nh * sizeof(double2);
     if (tw_bytes + plane_bytes > (size_t)TC_NOALLOC_SCRATCH_BYTES) {
-        tc_set_error_message("tc_to_physical_noalloc: (3 Nz/2) x (Ntheta/2) complex plane plus twiddles needs " +
+        tc_set_error_message("tc_to_physical_noalloc: one (3 Nz/2) x (Ntheta/2) complex plane plus twiddles needs " +
                              std::to_string(tw_bytes + plane_bytes) + " bytes, more than the " +
                              std::to_string((size_t)TC_NOALLOC_SCRATCH_BYTES) + "-byte scratch");
         return TC_ERR_SIZE;
@@ -122,24 +177,25 @@ extern "C" int tc_to_physical_noalloc(int Nr, int Ntheta, int Nz, const void* sp
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // The twiddles are rewritten on every call; the plane buffer is fully
-    // written by the z transform before the row transform reads it, so nothing
-    // has to start at zero.
-    cudaError_t e = cudaMemcpyAsync(scratch, tw.data(), (nz + nt) * sizeof(double2), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-        tc_set_error_message(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-        return TC_ERR_CUDA;
-    }
-    d.twz_d = reinterpret_cast<const double2*>(scratch);
-    d.twt_d = reinterpret_cast<const double2*>(scratch) + nz;
+    // Every call rewrites the twiddles, and the z transform fully writes each
+    // plane before the theta transform reads it, so nothing in the array has
+    // to start at zero.
+    double2* twz = reinterpret_cast<double2*>(scratch);
+    double2* twt = twz + nz;
+    k_noalloc_twiddles<<<d.pz.nst > 0 ? d.pz.nst : 1, 128, 0, s>>>(d.pz, twz);
+    k_noalloc_twiddles<<<d.pt.nst > 0 ? d.pt.nst : 1, 128, 0, s>>>(d.pt, twt);
+    d.twz_d = twz;
+    d.twt_d = twt;
     d.zbuf = scratch + tw_bytes;
+    const int chunk = (int)std::min<size_t>((size_t)Nr, ((size_t)TC_NOALLOC_SCRATCH_BYTES - tw_bytes) / plane_bytes);
     const double2* spec = static_cast<const double2*>(spectral_dev);
     double* phys = static_cast<double*>(physical_dev);
-    for (int r = 0; r < Nr; ++r) {
-        d.phys = phys + (size_t)r * d.Mz * d.Mt;
-        tc_launch_to_physical(d, spec + (size_t)r * d.Nz * d.Nh, s);
+    for (int r0 = 0; r0 < Nr; r0 += chunk) {
+        d.Nr = std::min(chunk, Nr - r0);
+        d.phys = phys + (size_t)r0 * d.Mz * d.Mt;
+        tc_launch_to_physical(d, spec + (size_t)r0 * d.Nz * d.Nh, s);
     }
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         tc_set_error_message(std::string("kernel launch: ") + cudaGetErrorString(e));
         return TC_ERR_CUDA;

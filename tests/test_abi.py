@@ -60,3 +60,27 @@ def test_device_byte_estimate_on_host(lib):
     # the 257 x 512 x 512 case: 11 spectral fields, 8 plane buffers, 8.5 tables per point
     P = 257 * 512 * 256
     assert b_big > P * (11 * 16 + 8 * 16 * 1.5 + 37 * 8)
+
+
+@pytest.mark.parametrize("Ntheta, Nz", [(4, 4374), (6144, 4)])
+def test_noalloc_rejects_transform_lengths_beyond_shared_memory(lib, Ntheta, Nz):
+    """3 Nz/2 = 6561 (one z column of 2 x 6561 complex values is 210 KB) and
+    3 Ntheta/2 = 9216 (295 KB) exceed the 200 KB a transform block may use;
+    both planes fit the fixed array, so only the shared-memory check can
+    refuse them, and it does so before any device call."""
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_to_physical_noalloc(1, Ntheta, Nz, 1, 1, None)
+    assert e.value.code == tc.TC_ERR_SIZE
+    assert "shared memory" in str(e.value)
+
+
+def test_noalloc_argument_checks_on_host(lib):
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_to_physical_noalloc(4, 20, 16, 1, 1, None)      # Ntheta = 20 is not 2^a 3^b
+    assert e.value.code == tc.TC_ERR_ARG
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_to_physical_noalloc(4, 16, 38, 1, 1, None)      # Nz = 38 has the factor 19
+    assert e.value.code == tc.TC_ERR_ARG
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_to_physical_noalloc(4, 16, 16, None, 1, None)
+    assert e.value.code == tc.TC_ERR_ARG

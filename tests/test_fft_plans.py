@@ -82,3 +82,68 @@ def test_compile_time_plans_match_host_plans(tmp_path):
     assert p.returncode == 0, p.stderr[-3000:]
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout[-3000:] + r.stderr[-2000:]
+
+
+TWIDDLES = r"""
+#include <cmath>
+#include <cstdio>
+#include <vector>
+#include "tc_internal.h"
+bool tc_build_fft_plan(int M, FftPlan& p, std::vector<long double>& re, std::vector<long double>& im, int family);
+
+int main() {
+    int bad = 0, lengths = 0;
+    for (int M = 6; M <= 6561; ++M) {
+        for (int F : {0, 1}) {
+            FftPlan p;
+            std::vector<long double> re, im;
+            if (!tc_build_fft_plan(M, p, re, im, F)) continue;
+            ++lengths;
+            int total = 0;
+            for (int s = 0; s < p.nst; ++s) {
+                long long num, den;
+                const int count = fft_twiddle_fraction(p, s, 0, num, den);
+                if (p.twoff[s] != total) { printf("M=%d F=%d stage %d offset\n", M, F, s); ++bad; }
+                for (int i = 0; i < count; ++i) {
+                    fft_twiddle_fraction(p, s, i, num, den);
+                    const long double a = -2.0L * 3.141592653589793238462643383279503L * (long double)num / (long double)den;
+                    const int k = p.twoff[s] + i;
+                    if (num < 0 || num >= den || k >= (int)re.size() ||
+                        fabsl(cosl(a) - re[k]) > 1e-17L || fabsl(sinl(a) - im[k]) > 1e-17L) {
+                        if (bad < 10) printf("M=%d F=%d stage %d entry %d\n", M, F, s, i);
+                        ++bad;
+                    }
+                }
+                total += count;
+            }
+            if (total != p.ntw || (int)re.size() != p.ntw) { printf("M=%d F=%d table size\n", M, F); ++bad; }
+        }
+    }
+    printf("%d plans\n", lengths);
+    printf(bad ? "FAIL %d\n" : "OK\n", bad);
+    return bad ? 1 : 0;
+}
+"""
+
+
+def test_device_twiddle_layout_matches_host_tables(tmp_path):
+    """The allocation-free transform computes its twiddle tables on the
+    device from (num, den) fractions of a turn (fft_twiddle_fraction in
+    csrc/tc_internal.h); every entry of every plan of both families, for all
+    lengths 6..6561 that have a plan, must be the entry the host plan builder
+    writes."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    if not os.path.exists(LIB):
+        pytest.skip("libtc.so not built")
+    src = tmp_path / "tw.cu"
+    src.write_text(TWIDDLES)
+    exe = tmp_path / "tw"
+    cmd = [nvcc, "-std=c++17", "-O1", "-gencode", "arch=compute_103a,code=sm_103a",
+           "-I", os.path.join(PKG, "csrc"), "-I", os.path.join(ROOT, "include"),
+           str(src), "-o", str(exe), "-L", PKG, "-ltc", f"-Xlinker=-rpath,{PKG}"]
+    p = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-3000:]
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("OK"), r.stdout[-3000:] + r.stderr[-2000:]
