@@ -46,10 +46,14 @@ def parse():
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--sample-planes", type=int, default=4)
     p.add_argument("--sample-pairs", type=int, default=1024)
+    p.add_argument("--sample-repeat", type=int, default=1)
     p.add_argument("--ncases", type=int, default=64, help="batch64: number of cases")
     p.add_argument("--serve-seconds", type=float, default=2.0, help="served: arrival window (s)")
     p.add_argument("--serve-rate", type=float, default=20.0, help="served: Poisson rate (1/s)")
     p.add_argument("--budget-gb", type=float, default=150.0, help="served: device budget")
+    p.add_argument("--torque-steps", type=int, default=500,
+                   help="steps of the torque run of the fp64 and mixed forms (0: none)")
+    p.add_argument("--no-many-cases", action="store_true", help="skip the batch64 and served results")
     p.add_argument("--column-groups", type=int, default=0,
                    help="pin the column groups of the step graph (0: chosen by timing)")
     return p.parse_args()
@@ -164,11 +168,19 @@ def algorithmic(w, prec):
 # ---------------------------------------------------------------------------
 def cpu_sample(args):
     """Time the oracle (as it stands) on a bounded sample of the workload and
-    extrapolate to grid-point steps per second.  Sample: the plane phase
-    (products with the 3/2 rule) on `sample_planes` radial planes and the
-    line phase (reconstruction, explicit rows, right sides, banded solves) on
-    `sample_pairs` Fourier pairs, each for one substep; one step costs
+    extrapolate to grid-point steps per second.  The sample builds only what
+    it times, so that one process per core fits in host memory:
+      * plane phase: the products with the 3/2 rule (inverse transforms of u,
+        v, w, the six products, forward transforms and truncation) on
+        `sample_planes` radial planes of the workload's Ntheta x Nz grid;
+      * line phase: reconstruction, explicit rows, right sides and banded
+        solves of one substep for every pair of a case with the workload's
+        radial grid (Nr, radius ratio, Re) and a small Fourier box of about
+        `sample_pairs` pairs; the oracle's per-pair work does not depend on
+        the pair's wavenumbers.
+    Both are repeated `sample_repeat` times; one step of the workload costs
     3 (Nr t_plane + npairs t_pair)."""
+    import math
     import numpy as np
     from oracle.grid import Case
     from oracle.rk import OracleSolver
@@ -177,50 +189,104 @@ def cpu_sample(args):
     w = WORKLOADS[args.workload]
     cs = Case(w["Nr"], w["Ntheta"], w["Nz"], w["zeta"], w["Re_i"], w["Re_o"], w["dt"])
     m0, a0, rc = box_defaults(w["zeta"])
-    v, e = initial_perturbation(w["Nr"], w["Ntheta"], w["Nz"], w["seed"], w["spectrum"], w["amp"],
-                                m0=m0, alpha0=a0, rc=rc)
-    rng = np.random.default_rng(0)
     K = min(args.sample_planes, cs.Nr)
-    sl = slice(cs.Nr // 2, cs.Nr // 2 + K)
-    t0 = time.perf_counter()
-    products(cs, v[sl], v[sl], e[sl])
-    t_plane = (time.perf_counter() - t0) / K
-    mask = np.zeros((cs.Nz, cs.Nh), dtype=bool)
-    idx = rng.choice(cs.Nz * cs.Nh, size=min(args.sample_pairs, cs.Nz * cs.Nh), replace=False)
-    mask.flat[idx] = True
-    s = OracleSolver(cs, pairs=mask)
-    s.set_fields(v=v * mask, eta=e * mask)
+    vp, ep = initial_perturbation(K + 2, w["Ntheta"], w["Nz"], w["seed"], w["spectrum"], w["amp"],
+                                  m0=m0, alpha0=a0, rc=rc)
+    vp, ep = vp[1:-1], ep[1:-1]
+    side = 1 << max(2, int(round(math.log2(max(4, args.sample_pairs)) / 2)))
+    cl = Case(w["Nr"], 2 * side, side, w["zeta"], w["Re_i"], w["Re_o"], w["dt"])
+    vl, el = initial_perturbation(cl.Nr, cl.Ntheta, cl.Nz, w["seed"], w["spectrum"], w["amp"],
+                                  m0=m0, alpha0=a0, rc=rc)
+    s = OracleSolver(cl)
+    s.set_fields(v=vl, eta=el)
     npairs = len(s.act[0])
-    P = {k: np.zeros_like(v) for k in ("uu", "uv", "uw", "vv", "vw", "ww")}
-    t0 = time.perf_counter()
-    s.advance(0, s.explicit_terms(P))
-    t_pair = (time.perf_counter() - t0) / npairs
+    P = {k: np.zeros_like(vl) for k in ("uu", "uv", "uw", "vv", "vw", "ww")}
+    t_plane = t_pair = 0.0
+    reps = max(1, args.sample_repeat)
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        products(cs, vp, vp, ep)
+        t_plane += (time.perf_counter() - t0) / K / reps
+        t0 = time.perf_counter()
+        s.advance(0, s.explicit_terms(P))
+        t_pair += (time.perf_counter() - t0) / npairs / reps
     total_pairs = int(cs.active_mask().sum())
     t_step = 3.0 * (cs.Nr * t_plane + total_pairs * t_pair)
     return {"value": cs.gridpoints / t_step, "t_step_s": t_step, "t_plane_s": t_plane,
-            "t_pair_s": t_pair, "planes": K, "pairs": npairs,
-            "sample": f"oracle plane phase on {K} of {cs.Nr} radial planes and line phase on {npairs} "
-                      f"of {total_pairs} Fourier pairs, one substep each, extrapolated to a full "
-                      f"3-substep step of {args.workload}"}
+            "t_pair_s": t_pair, "planes": K, "pairs": npairs, "repeat": reps,
+            "sample": f"oracle plane phase on {K} radial planes of {w['Ntheta']} x {w['Nz']} modes and line "
+                      f"phase on the {npairs} pairs of a {cl.Ntheta} x {cl.Nz}-mode case with the same "
+                      f"{cs.Nr}-point radial grid, one substep each, repeated {reps} times, extrapolated to a "
+                      f"full 3-substep step of {args.workload} ({cs.Nr} planes, {total_pairs} pairs)"}
 
 
-def run_cpu_sample_subprocess(args, threads=1):
+def _sample_cmd(args):
+    return [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
+            "--sample-planes", str(args.sample_planes), "--sample-pairs", str(args.sample_pairs),
+            "--sample-repeat", str(args.sample_repeat)]
+
+
+def _sample_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = str(threads)
-    env.pop("WORLD_SIZE", None)
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
-           "--sample-planes", str(args.sample_planes), "--sample-pairs", str(args.sample_pairs)]
-    p = subprocess.run(cmd, capture_output=True, text=True, env=env)
+        env[k] = "1"
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        env.pop(k, None)
+    return env
+
+
+def run_cpu_sample_subprocess(args):
+    """One oracle process, one thread."""
+    p = subprocess.run(_sample_cmd(args), capture_output=True, text=True, env=_sample_env())
     if p.returncode != 0:
         raise RuntimeError(p.stderr[-2000:])
     res = json.loads(p.stdout.strip().splitlines()[-1])
-    res["cores"] = threads
+    res["cores"] = 1
     return res
+
+
+def run_cpu_sample_all_cores(args, ncores=None):
+    """One single-threaded oracle process per host core, all at once, each on
+    the sample above.  The oracle's planes and pairs are independent, so the
+    cores would share a step's work; the rate of all cores together is
+    ncores x gridpoints / (the slowest process's extrapolated step time)."""
+    ncores = ncores or os.cpu_count() or 1
+    procs = [subprocess.Popen(_sample_cmd(args), stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=_sample_env()) for _ in range(ncores)]
+    res = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    t_max = max(r["t_step_s"] for r in res)
+    gp = res[0]["value"] * res[0]["t_step_s"]
+    return {"value": ncores * gp / t_max, "t_step_s": t_max / ncores, "cores": ncores,
+            "per_process_t_step_s": [round(r["t_step_s"], 3) for r in res],
+            "sample": res[0]["sample"] + f"; {ncores} such processes at once, one per core"}
+
+
+def state_bytes_floor(w):
+    """Bytes of the six spectral fields every form keeps resident (v, eta, u,
+    w and the two RK memories), a lower bound of the step's working set."""
+    P = w["Nr"] * w["Nz"] * (w["Ntheta"] // 2)
+    return 6 * P * 16
+
+
+def config_of(args, w, world):
+    """The config dict of the bench line, shared by both arms."""
+    sb = state_bytes_floor(w)
+    return {"workload": args.workload, "Nr": w["Nr"], "Ntheta": w["Ntheta"], "Nz": w["Nz"],
+            "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
+            "precision": args.precision, "parallelism": f"replicas{world}",
+            "l2": (f"inputs larger than L2 (resident spectral state >= {sb / 1e9:.1f} GB), not flushed"
+                   if sb > 129e6 else "state may fit in L2 (not flushed)")}
 
 
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle on the machine's host cores: every step is one all-core sample
+    (one process per core, as above), extrapolated to a full step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -229,18 +295,23 @@ def run_reference(args):
     vals = []
     t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        r = run_cpu_sample_subprocess(args)
+        r = run_cpu_sample_all_cores(args)
         if i >= args.warmup:
             vals.append(r)
     wall = time.perf_counter() - t_all
     t_step = statistics.mean(x["t_step_s"] for x in vals)
     value = (w["Nr"] * w["Ntheta"] * w["Nz"]) / t_step
+    cores = vals[0]["cores"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": args.workload, "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "impl": "reference", "config": config_of(args, w, world),
+            "extrapolated": True,
+            "extrapolation": (f"each of the {args.steps} timed steps is one sample of the oracle on all "
+                              f"{cores} host cores (per process: one substep of the plane phase on "
+                              f"{args.sample_planes} planes and of the line phase on ~{args.sample_pairs} "
+                              f"pairs), scaled to the full 3-substep step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -248,9 +319,12 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False):
+def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False, torque_steps=0):
     """Create the case in one precision form, warm up, time K steps with CUDA
-    events on the launch stream, then time each kernel (tc_phase_times)."""
+    events on the launch stream, then time each kernel (tc_phase_times).
+    With torque_steps > 0, the state is then reset to the initial condition
+    and run for torque_steps steps, recording the torques after every step
+    (outside the timed region)."""
     Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
     h = tc.tc_create_ex(Nr, Nt, Nz, w["zeta"], w["Re_i"], w["Re_o"], w["dt"], precision=prec, device=local,
                         autotune=1)
@@ -258,6 +332,7 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False)
     tc.tc_set_stream(h, stream.cuda_stream)
     tc.tc_set_field(h, tc.TC_FIELD_V, v)
     tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
+    W0 = tc.tc_get_field(h, tc.TC_FIELD_MEAN_W)
     if args.column_groups:
         tc.tc_set_tiles(h, 0, 0, args.column_groups)
     tc.tc_step(h, max(args.warmup, 3))
@@ -282,8 +357,29 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False)
              "W": tc.tc_get_field(h, tc.TC_FIELD_MEAN_W), "U": tc.tc_get_field(h, tc.TC_FIELD_MEAN_U)}
     torque = tc.tc_torque_stats(h)
     ph = tc.tc_phase_times(h, 1)
+    series = None
+    if torque_steps > 0:
+        import numpy as np
+        tc.tc_set_field(h, tc.TC_FIELD_V, v)
+        tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
+        tc.tc_set_field(h, tc.TC_FIELD_MEAN_W, W0)
+        tc.tc_set_field(h, tc.TC_FIELD_MEAN_U, np.zeros_like(W0))
+        series = {"G_inner": [], "G_outer": [], "energy": []}
+        for _ in range(torque_steps):
+            tc.tc_step(h, 1)
+            st = tc.tc_torque_stats(h)
+            for k in series:
+                series[k].append(st[k])
     return h, {"total_ms": total_ms, "per": per, "clk": clk, "state": state, "phase_ms": ph,
-               "torque": torque}
+               "torque": torque, "series": series}
+
+
+def torque_summary(series):
+    import numpy as np
+    g, go = np.array(series["G_inner"]), np.array(series["G_outer"])
+    return {"steps": len(g), "G_inner_mean": float(g.mean()), "G_outer_mean": float(go.mean()),
+            "G_inner_first": float(g[0]), "G_inner_last": float(g[-1]),
+            "energy_last": float(series["energy"][-1])}
 
 
 # DRAM bytes per z row of k_rows<double> (Ntheta = 512, Mt = 768): one ncu
@@ -354,7 +450,9 @@ def run_gpu(args):
     v, e = initial_perturbation(Nr, Nt, Nz, w["seed"] + rank, w["spectrum"], w["amp"], m0=m0, alpha0=a0, rc=rc)
     peaks = tc.tc_fma_peak(local)
 
-    h, main = time_form(tc, torch, w, PREC[args.precision], v, e, args, local, dist, measure_clocks=True)
+    tq = args.torque_steps if args.precision in ("fp64", "mixed") else 0
+    h, main = time_form(tc, torch, w, PREC[args.precision], v, e, args, local, dist, measure_clocks=True,
+                        torque_steps=tq)
     value = gp * args.steps * world / (main["total_ms"] / 1e3)
     per = main["per"]
     p50 = statistics.median(per)
@@ -396,11 +494,15 @@ def run_gpu(args):
 
     # ---- the other precision forms, same input and step count; error against this run
     forms = {}
+    series = {args.precision: main["series"]} if main["series"] else {}
     if not args.no_forms:
         ref = main["state"]
         for name in [p for p in ("df64", "mixed", "fp64") if p != args.precision]:
-            hf, res = time_form(tc, torch, w, PREC[name], v, e, args, local, dist)
+            hf, res = time_form(tc, torch, w, PREC[name], v, e, args, local, dist,
+                                torque_steps=args.torque_steps if name in ("fp64", "mixed") else 0)
             tc.tc_destroy(hf)
+            if res["series"]:
+                series[name] = res["series"]
             err = {k: float(np.linalg.norm(res["state"][k] - ref[k]) / np.linalg.norm(ref[k]))
                    for k in ("v", "eta", "W")}
             err["U"] = float(np.linalg.norm(res["state"]["U"] - ref["U"]) / max(np.linalg.norm(ref["U"]), 1e-300))
@@ -415,12 +517,17 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import argparse as _ap
+        sargs = _ap.Namespace(**vars(args))
+        sargs.sample_repeat = max(args.sample_repeat, 3)
         try:
-            cpu = run_cpu_sample_subprocess(args)
-            cpu = {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
-                   "sample": cpu["sample"]}
+            allc = run_cpu_sample_all_cores(sargs)
+            one = run_cpu_sample_subprocess(sargs)
+            cpu = {"value": allc["value"], "unit": UNIT, "cores": allc["cores"], "kind": "oracle",
+                   "sample": allc["sample"],
+                   "single_core": {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}}
         except Exception as ex:        # reported, not fatal
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(ex)[-300:]}
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "error": str(ex)[-300:]}
 
     # ---- the paper's own timed workload (Sec. 3.1: 182 s per step on one
     # 2.66 GHz Xeon, i.e. 129 x 512 x 170 / 182 = 6.17e4 grid-point steps/s)
@@ -440,21 +547,34 @@ def run_gpu(args):
             paper["forms"][name] = {"value": val, "ms_per_step": res["total_ms"] / args.steps,
                                     "vs_paper": val / 6.17e4, "dtype": DTYPE[name]}
 
+    torque_run = None
+    if "fp64" in series and "mixed" in series:
+        import numpy as np
+        gf, gm = np.array(series["fp64"]["G_inner"]), np.array(series["mixed"]["G_inner"])
+        torque_run = {"what": f"inner/outer torque G (Eq. 2, Table 2 reading) after each of "
+                              f"{len(gf)} steps from the initial condition, mean over the run",
+                      "fp64": torque_summary(series["fp64"]), "mixed": torque_summary(series["mixed"]),
+                      "rel_diff_G_inner_mean": float(abs(gm.mean() - gf.mean()) / gf.mean()),
+                      "max_rel_diff_G_inner_per_step": float(np.max(np.abs(gm - gf) / gf))}
+
+    many = None
+    if not args.no_many_cases and args.workload == "tc-257x512x512" and world == 1:
+        many = {"batch64": {}, "served": {}}
+        for name in ("fp64", "mixed"):
+            many["batch64"][name] = batch_measure(args, tc, torch, name, local, dist)
+            many["served"][name] = served_measure(args, tc, torch, name, local)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": main["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": args.workload, "Nr": Nr, "Ntheta": Nt, "Nz": Nz,
-                       "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
-                       "precision": args.precision, "parallelism": f"replicas{world}",
-                       "l2": (f"inputs larger than L2 (state {device_bytes / 1e9:.1f} GB)"
-                              if device_bytes > 129e6 else "state fits in L2 (not flushed)"),
-                       "device_bytes": device_bytes},
+            "config": config_of(args, w, world), "device_bytes": device_bytes,
             "latency_ms": {"p50": p50, "p99": p99},
             "gpu_launches": tc.step_kernels(ch) * args.steps,
             "launch_shapes": {"ztile": zt, "line_variant": lv, "column_groups": ch},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clk"],
-            "alu_peaks_tflops": peaks, "forms": forms, "paper_workload": paper}
+            "alu_peaks_tflops": peaks, "forms": forms, "paper_workload": paper,
+            "torque_run": torque_run, "many_cases": many}
     if rank == 0:
         print(json.dumps(line))
     dist.close()
@@ -486,14 +606,12 @@ def ensemble_ic(spec):
     return initial_perturbation(Nr, Nt, Nz, seed, "k2", 0.05, m0=m0, alpha0=a0, rc=rc)
 
 
-def run_batch(args):
+def batch_measure(args, tc, torch, prec_name, local, dist):
+    """The batched ensemble: args.ncases independent cases stepped together,
+    K timed steps after W warm-up steps; returns the result dict."""
     import numpy as np
-    import torch
-    import paper_0711_1429_gb300 as tc
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = Dist(world, rank, "nccl")
-    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[args.precision]
+    world, rank, _ = dist_env()
+    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[prec_name]
     rng = np.random.default_rng(1000 + rank)
     cases = [ensemble_case(rng, i, prec) for i in range(args.ncases)]
     for p, _ in cases:
@@ -524,29 +642,43 @@ def run_batch(args):
     clk = clocks.stop()
     per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
     total = dist.max(ev[0].elapsed_time(ev[args.steps]))
-    line = {"metric": METRIC, "value": gp * args.steps * world / (total / 1e3), "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
-            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": f"batch{args.ncases}", "cases": args.ncases, "gridpoints": gp,
-                       "precision": args.precision, "graph": "one CUDA graph per step, one branch per case",
-                       "autotune": True, "device_bytes": tc.tc_batch_device_bytes(b)},
-            "latency_ms": {"p50": statistics.median(per), "p99": per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]},
-            "gpu_launches": 15 * args.ncases * args.steps, "clocks": clk}
+    launches = 15 * args.ncases          # one 15-kernel step graph branch per case
+    res = {"value": gp * args.steps * world / (total / 1e3), "unit": UNIT,
+           "ms_per_step": total / args.steps, "steps": args.steps, "warmup": max(args.warmup, 3),
+           "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[prec_name],
+           "cases": args.ncases, "gridpoints": gp, "device_bytes": tc.tc_batch_device_bytes(b),
+           "latency_ms": {"p50": statistics.median(per),
+                          "p99": per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]},
+           "gpu_launches": launches * args.steps, "clocks": clk}
     tc.tc_batch_destroy(b)
+    return res
+
+
+def run_batch(args):
+    import torch
+    import paper_0711_1429_gb300 as tc
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = Dist(world, rank, "nccl")
+    r = batch_measure(args, tc, torch, args.precision, local, dist)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic",
+            "config": {"workload": f"batch{args.ncases}", "cases": args.ncases, "gridpoints": r["gridpoints"],
+                       "precision": args.precision, "autotune": True},
+            "device_bytes": r["device_bytes"], "latency_ms": r["latency_ms"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
     if rank == 0:
         print(json.dumps(line))
     dist.close()
 
 
-def run_served(args):
+def served_measure(args, tc, torch, prec_name, local):
+    """The served stream: Poisson arrivals over the window, each request
+    submitted at its arrival time; returns the result dict."""
     import numpy as np
-    import torch
-    import paper_0711_1429_gb300 as tc
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[args.precision]
+    world, rank, _ = dist_env()
+    prec = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}[prec_name]
     rng = np.random.default_rng(7 + rank)
     # Poisson arrivals over the window, cases as the ensemble plus 5% 257 x 256 x 256
     t, arrivals = 0.0, []
@@ -581,18 +713,33 @@ def run_served(args):
     tc.tc_server_destroy(s)
     bad = [r for r in res if r["status"] != tc.TC_OK]
     nsteps = sum(n for _, _, _, n in arrivals)
-    line = {"metric": METRIC, "value": st["gridpoint_steps"] / (st["busy_ms"] / 1e3), "unit": UNIT,
-            "n_gpus": 1, "steps": int(st["steps"]), "warmup": 0, "ms_per_step": st["busy_ms"] / max(1, nsteps),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[args.precision], "data": "synthetic",
-            "config": {"workload": "served", "requests": len(arrivals), "rate_per_s": args.serve_rate,
-                       "window_s": args.serve_seconds, "budget_gb": args.budget_gb,
-                       "precision": args.precision, "peak_active": st["peak_active"],
-                       "peak_used_gb": st["peak_used_bytes"] / 1e9, "failed": len(bad)},
+    return {"value": st["gridpoint_steps"] / (st["busy_ms"] / 1e3), "unit": UNIT,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[prec_name],
+            "requests": len(arrivals), "steps": int(st["steps"]), "rate_per_s": args.serve_rate,
+            "window_s": args.serve_seconds, "budget_gb": args.budget_gb,
+            "peak_active": st["peak_active"], "peak_used_gb": st["peak_used_bytes"] / 1e9,
+            "within_budget": st["peak_used_bytes"] <= st["budget_bytes"], "failed": len(bad),
             "latency_ms": {"p50": st["step_ms_p50"], "p99": st["step_ms_p99"]},
+            "busy_s": st["busy_ms"] / 1e3, "wall_s": wall,
             "e2e": {"value": st["gridpoint_steps"] / wall, "unit": UNIT,
                     "h2d_bytes_per_step": h2d / max(1, nsteps), "d2h_bytes_per_step": d2h / max(1, nsteps)},
-            "gpu_launches": 15 * int(st["steps"]), "clocks": clk, "wall_s": wall}
+            "clocks": clk}
+
+
+def run_served(args):
+    import torch
+    import paper_0711_1429_gb300 as tc
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    r = served_measure(args, tc, torch, args.precision, local)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+            "warmup": 0, "ms_per_step": r["busy_s"] * 1e3 / max(1, r["steps"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"],
+            "data": "synthetic",
+            "config": {"workload": "served", "requests": r["requests"], "rate_per_s": args.serve_rate,
+                       "window_s": args.serve_seconds, "budget_gb": args.budget_gb, "precision": args.precision},
+            "peak_active": r["peak_active"], "peak_used_gb": r["peak_used_gb"], "failed": r["failed"],
+            "latency_ms": r["latency_ms"], "e2e": r["e2e"], "clocks": r["clocks"], "wall_s": r["wall_s"]}
     if rank == 0:
         print(json.dumps(line))
 

@@ -32,8 +32,15 @@ def test_reference_arm_prints_one_contract_line():
     gp = 33 * 16 * 16
     assert abs(line["value"] * line["ms_per_step"] / 1e3 - gp) < 1e-6 * gp
     cpu = line["cpu_baseline"]
-    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] == line["value"]
-    assert "1 of 33 radial planes" in cpu["sample"] and "8 of" in cpu["sample"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] == (os.cpu_count() or 1) and cpu["value"] == line["value"]
+    assert "1 radial planes of 16 x 16 modes" in cpu["sample"] and "one per core" in cpu["sample"]
+    assert line["extrapolated"] is True
+    # the same config keys and values as the GPU arm's line (bench.config_of)
+    cfg = line["config"]
+    assert cfg["workload"] == "tc-small-33x16x16" and cfg["Nr"] == 33 and cfg["Ntheta"] == 16 and cfg["Nz"] == 16
+    assert cfg["precision"] == "fp64" and cfg["parallelism"] == "replicas1"
+    assert set(cfg) == {"workload", "Nr", "Ntheta", "Nz", "radius_ratio", "Re_inner", "dt", "precision",
+                        "parallelism", "l2"}
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
