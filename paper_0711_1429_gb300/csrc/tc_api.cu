@@ -396,7 +396,13 @@ int init_handle(tc_handle* h) {
     d.npairs = d.Nz * d.Nh;
     d.mixed = P.precision == TC_PREC_MIXED ? 1 : 0;
     d.prec = P.precision;
-    d.ztile = d.Nh % 8 == 0 ? 8 : (d.Nh % 4 == 0 ? 4 : (d.Nh % 2 == 0 ? 2 : 1));
+    // widest z tile (azimuthal columns per block) that divides Ntheta/2 and
+    // whose two Mz-long complex columns per tile fit the 200 KB of shared
+    // memory a block may use
+    d.ztile = 1;
+    for (int t : {8, 4, 2}) {
+        if (d.Nh % t == 0 && 2 * (size_t)t * d.Mz * sizeof(double2) <= 200 * 1024) { d.ztile = t; break; }
+    }
     d.line_block = 128;
     d.fscale = 1.0 / ((double)d.Mt * (double)d.Mz);
     d.fscale_f = (float)d.fscale;
@@ -756,6 +762,17 @@ int validate(const tc_params* p) {
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) { set_err("dt must be > 0"); return TC_ERR_ARG; }
     if (!(p->stretch >= 0.0 && p->stretch <= 8.0)) { set_err("stretch must lie in [0, 8]"); return TC_ERR_ARG; }
     if (p->precision != TC_PREC_FP64 && p->precision != TC_PREC_MIXED && p->precision != TC_PREC_DF64) { set_err("unknown precision"); return TC_ERR_ARG; }
+    // shared memory of one block (at most 200 KB): a z transform holds two
+    // complex columns of 3 Nz/2 values (16 bytes each in the float64 and
+    // double-float forms), a theta row 4 (double-float: 5) complex rows of
+    // 3 Ntheta/2 values
+    const size_t Mz = 3 * (size_t)p->Nz / 2, Mt = 3 * (size_t)p->Ntheta / 2, lim = 200 * 1024;
+    const size_t row_bytes = (p->precision == TC_PREC_DF64 ? 5 : 4) * Mt * (p->precision == TC_PREC_MIXED ? 8 : 16);
+    if (2 * Mz * 16 > lim || row_bytes > lim || 2 * Mt * 16 > lim) {
+        set_err("grid too large for the shared memory of one transform block: Nz <= 4266, Ntheta <= " +
+                std::string(p->precision == TC_PREC_DF64 ? "1706" : p->precision == TC_PREC_MIXED ? "4266" : "2133"));
+        return TC_ERR_SIZE;
+    }
     return TC_OK;
 }
 

@@ -31,6 +31,8 @@ def test_exports_every_declared_function(lib):
     ((33, 16, 16, 1.0, 200.0, 0.0, 1e-3), "radius ratio"),
     ((33, 16, 16, 0.5, -1.0, 0.0, 1e-3), "Re_inner"),
     ((33, 16, 16, 0.5, 100.0, 0.0, 0.0), "dt"),
+    ((9, 16, 4374, 0.883, 200.0, 0.0, 1e-3), "shared memory"),     # z columns of 6561 points
+    ((9, 3072, 16, 0.883, 200.0, 0.0, 1e-3), "shared memory"),     # float64 theta rows of 4608 points
 ])
 def test_invalid_arguments_are_rejected(lib, args, msg):
     with pytest.raises(tc.TcError) as e:
