@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--torque-steps", type=int, default=500,
                    help="steps of the torque run of the fp64 and mixed forms (0: none)")
     p.add_argument("--no-many-cases", action="store_true", help="skip the batch64 and served results")
+    p.add_argument("--nr", type=int, default=0,
+                   help="radial points instead of the workload's (profiling captures of the per-pair "
+                        "kernels at the full pair count with a smaller device footprint)")
     p.add_argument("--column-groups", type=int, default=0,
                    help="pin the column groups of the step graph (0: chosen by timing)")
     return p.parse_args()
@@ -276,7 +279,8 @@ def state_bytes_floor(w):
 def config_of(args, w, world):
     """The config dict of the bench line, shared by both arms."""
     sb = state_bytes_floor(w)
-    return {"workload": args.workload, "Nr": w["Nr"], "Ntheta": w["Ntheta"], "Nz": w["Nz"],
+    name = args.workload if not getattr(args, "nr", 0) else f"{args.workload} with Nr = {args.nr}"
+    return {"workload": name, "Nr": w["Nr"], "Ntheta": w["Ntheta"], "Nz": w["Nz"],
             "radius_ratio": w["zeta"], "Re_inner": w["Re_i"], "dt": w["dt"],
             "precision": args.precision, "parallelism": f"replicas{world}",
             "l2": (f"inputs larger than L2 (resident spectral state >= {sb / 1e9:.1f} GB), not flushed"
@@ -383,13 +387,11 @@ def torque_summary(series):
 
 
 # DRAM bytes per z row of k_rows<double> (Ntheta = 512, Mt = 768): one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) on the paper workload
-# 129 x 512 x 170, 32895 rows per launch; the per-row traffic does not depend
-# on Nr or Nz.  The kernel has changed since (forward plan order and the
-# products' scale factor; the same global loads and stores), so the figure is
-# reported beside the roofline, not as its measured traffic.
-ROWS_FP64_BYTES_PER_ROW = {512: (404830720 + 627351040) / 32895}
-ROWS_FP64_CAPTURE_CURRENT = False
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
+# kernel on the paper workload 129 x 512 x 170, 32895 rows per launch; the
+# per-row traffic does not depend on Nr or Nz.
+ROWS_FP64_BYTES_PER_ROW = {512: (404588032 + 622788864) / 32895}
+ROWS_FP64_CAPTURE_CURRENT = True
 
 
 def roofline_of(w, prec_name, ph, peaks):
@@ -429,6 +431,14 @@ def roofline_of(w, prec_name, ph, peaks):
     return roof
 
 
+def workload_of(args):
+    from paper_0711_1429_gb300.synthetic import WORKLOADS
+    w = dict(WORKLOADS[args.workload])
+    if args.nr:
+        w["Nr"] = args.nr
+    return w
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -441,7 +451,7 @@ def run_gpu(args):
     if not os.path.exists(tc.LIB_PATH):
         from paper_0711_1429_gb300 import build as b
         b.build()
-    w = WORKLOADS[args.workload]
+    w = workload_of(args)
     PREC = {"fp64": tc.TC_PREC_FP64, "mixed": tc.TC_PREC_MIXED, "df64": tc.TC_PREC_DF64}
     DTYPE = {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}
     Nr, Nt, Nz = w["Nr"], w["Ntheta"], w["Nz"]
