@@ -652,7 +652,7 @@ def batch_measure(args, tc, torch, prec_name, local, dist):
     clk = clocks.stop()
     per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps))
     total = dist.max(ev[0].elapsed_time(ev[args.steps]))
-    launches = 15 * args.ncases          # one 15-kernel step graph branch per case
+    launches = tc.tc_batch_launches_per_step(b)
     res = {"value": gp * args.steps * world / (total / 1e3), "unit": UNIT,
            "ms_per_step": total / args.steps, "steps": args.steps, "warmup": max(args.warmup, 3),
            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[prec_name],

@@ -234,15 +234,24 @@ size_t tc_estimate_device_bytes(const tc_params* params);
 
 /* Batch: ncases independent cases (params[i] each, any shapes and
  * precisions), each with its own resident state; tc_batch_step advances all
- * of them by nsteps steps with one CUDA-graph launch per step in which every
- * case is a concurrent branch.  Cases are reached with tc_batch_case for
- * tc_set_field / tc_get_field / tc_torque_stats; the handle stays owned by
- * the batch.  Results equal those of the same case stepped alone. */
+ * of them by nsteps steps with one CUDA-graph launch per step.  Cases of the
+ * same precision form, Ntheta and Nz make one shape class (any Nr, radius
+ * ratio, Re and box).  Per substep, each of the three plane-phase kernels is
+ * one launch per class covering all of its cases (the classes run as
+ * concurrent graph branches), then the line kernel and the mean flow are one
+ * launch each per precision form, covering all of its cases.  Cases are
+ * reached with tc_batch_case for tc_set_field / tc_get_field /
+ * tc_torque_stats; the handle stays owned by the batch.  Results equal those
+ * of the same case stepped alone, bit for bit.
+ * tc_batch_set_stream: the caller keeps ownership of the stream.
+ * tc_batch_launches_per_step: kernels one step launches,
+ * 3 x (3 x classes + 2 x forms). */
 typedef struct tc_batch tc_batch;
 tc_batch* tc_batch_create(int ncases, const tc_params* params);
 tc_handle* tc_batch_case(tc_batch* b, int i);
 int tc_batch_step(tc_batch* b, int nsteps);
 int tc_batch_set_stream(tc_batch* b, void* cuda_stream);
+int tc_batch_launches_per_step(const tc_batch* b);
 size_t tc_batch_device_bytes(const tc_batch* b);
 void tc_batch_destroy(tc_batch* b);
 

@@ -121,6 +121,8 @@ def lib():
     L.tc_batch_step.argtypes = [vp, i]
     L.tc_batch_set_stream.restype = i
     L.tc_batch_set_stream.argtypes = [vp, vp]
+    L.tc_batch_launches_per_step.restype = i
+    L.tc_batch_launches_per_step.argtypes = [vp]
     L.tc_batch_device_bytes.restype = sz
     L.tc_batch_device_bytes.argtypes = [vp]
     L.tc_batch_destroy.restype = None
@@ -351,6 +353,14 @@ def tc_batch_step(b, nsteps=1):
 
 def tc_batch_set_stream(b, stream_ptr):
     return _check(lib().tc_batch_set_stream(b, stream_ptr))
+
+
+def tc_batch_launches_per_step(b):
+    """Kernels one batch step launches: 3 x (3 x shape classes + 2 x precision forms)."""
+    n = lib().tc_batch_launches_per_step(b)
+    if n < 0:
+        _check(n)
+    return n
 
 
 def tc_batch_device_bytes(b):

@@ -6,6 +6,9 @@
 void tc_plane_kernel_f64(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles);
 void tc_plane_kernel_f32(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles);
 void tc_plane_kernel_df(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles);
+void tc_plane_kernel_batch_f64(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which, cudaStream_t s);
+void tc_plane_kernel_batch_f32(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which, cudaStream_t s);
+void tc_plane_kernel_batch_df(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which, cudaStream_t s);
 cudaError_t tc_plane_attributes_f64();
 cudaError_t tc_plane_attributes_f32();
 cudaError_t tc_plane_attributes_df();
@@ -42,6 +45,13 @@ void tc_launch_plane_kernel_tiles(const TcDev& d, int which, cudaStream_t s, int
     if (d.prec == 1) tc_plane_kernel_f32(d, which, s, tile0, ntiles);
     else if (d.prec == 2) tc_plane_kernel_df(d, which, s, tile0, ntiles);
     else tc_plane_kernel_f64(d, which, s, tile0, ntiles);
+}
+
+void tc_launch_plane_kernel_batch(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which,
+                                  cudaStream_t s) {
+    if (d0.prec == 1) tc_plane_kernel_batch_f32(d0, ds, ymap, nplanes, which, s);
+    else if (d0.prec == 2) tc_plane_kernel_batch_df(d0, ds, ymap, nplanes, which, s);
+    else tc_plane_kernel_batch_f64(d0, ds, ymap, nplanes, which, s);
 }
 
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s) {

@@ -6,3 +6,8 @@ void tc_plane_kernel_df(const TcDev& d, int which, cudaStream_t s, int tile0, in
 }
 
 cudaError_t tc_plane_attributes_df() { return plane_attributes_t<dfloat>(); }
+
+void tc_plane_kernel_batch_df(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which,
+                             cudaStream_t s) {
+    plane_kernel_batch_t<dfloat>(d0, ds, ymap, nplanes, which, s);
+}

@@ -6,3 +6,8 @@ void tc_plane_kernel_f32(const TcDev& d, int which, cudaStream_t s, int tile0, i
 }
 
 cudaError_t tc_plane_attributes_f32() { return plane_attributes_t<float>(); }
+
+void tc_plane_kernel_batch_f32(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which,
+                             cudaStream_t s) {
+    plane_kernel_batch_t<float>(d0, ds, ymap, nplanes, which, s);
+}

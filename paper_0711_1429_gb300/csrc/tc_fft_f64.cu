@@ -7,6 +7,11 @@ void tc_plane_kernel_f64(const TcDev& d, int which, cudaStream_t s, int tile0, i
 
 cudaError_t tc_plane_attributes_f64() { return plane_attributes_t<double>(); }
 
+void tc_plane_kernel_batch_f64(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which,
+                             cudaStream_t s) {
+    plane_kernel_batch_t<double>(d0, ds, ymap, nplanes, which, s);
+}
+
 // ---- physical output of one field (float64) ---------------------------------
 __global__ void __launch_bounds__(256) k_rows_phys(TcDev d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -23,7 +28,7 @@ __global__ void __launch_bounds__(256) k_rows_phys(TcDev d) {
         bufA[p] = a;
     }
     __syncthreads();
-    double2* res = fft_stockham<double, +1, 0>(bufA, bufB, 1, d.pt, d.twt_d);
+    double2* res = fft_stockham<double, +1, 0>(tg_block(), bufA, bufB, 1, d.pt, d.twt_d);
     for (int p = threadIdx.x; p < Mt; p += blockDim.x)
         d.phys[((size_t)r * Mz + q) * Mt + p] = res[p].x;
 }

@@ -44,6 +44,11 @@ template <> struct V2<double> { typedef double2 t; };
 template <> struct V2<float> { typedef float2 t; };
 template <> struct V2<dfloat> { typedef dcomplex t; };
 
+// The threads of a block that work on one transform group (a z tile, or one
+// theta row of a block that holds several): tid = 0 .. nth-1 within the group.
+struct TG { int tid, nth; };
+__device__ __forceinline__ TG tg_block() { return TG{(int)threadIdx.x, (int)blockDim.x}; }
+
 template <typename C> __device__ __forceinline__ C c_add(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
@@ -279,7 +284,7 @@ __device__ __forceinline__ void stockham_bfly_prime(const C* sc, C* dcol, int j,
 // c*M), with the plan chosen at run time.  Returns the buffer holding the
 // result (buf0 or buf1).
 template <typename T, int SIGN, int F = 1>
-__device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<T>::t* buf1,
+__device__ typename V2<T>::t* fft_stockham(const TG tg, typename V2<T>::t* buf0, typename V2<T>::t* buf1,
                                            int ncols, const FftPlan& pl,
                                            const typename V2<T>::t* __restrict__ tw) {
     typedef typename V2<T>::t C;
@@ -290,7 +295,7 @@ __device__ typename V2<T>::t* fft_stockham(typename V2<T>::t* buf0, typename V2<
         const int R = pl.R[s], Ns = pl.Ns[s];
         const int nb = M / R;
         const C* tws = tw + pl.twoff[s];
-        for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
+        for (int b = tg.tid; b < ncols * nb; b += tg.nth) {
             const int col = b / nb;
             const int j = b - col * nb;
             const C* sc = src + col * M;
@@ -383,7 +388,7 @@ __device__ __forceinline__ void stockham_bfly3_zero_mid(const C* sc, C* dcol, in
 }
 
 template <typename T, int SIGN, int M, int F, int S, bool Z0 = false>
-__device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t* src, typename V2<T>::t* dst,
+__device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(const TG tg, typename V2<T>::t* src, typename V2<T>::t* dst,
                                                               int ncols, const typename V2<T>::t* __restrict__ tw,
                                                               const double* __restrict__ twtan) {
     typedef typename V2<T>::t C;
@@ -395,7 +400,7 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
         constexpr int Ns = plan_ns_f(M, S, F);
         constexpr int nb = M / R;
         const C* tws = tw + plan_off_f(M, S, F);
-        for (int b = threadIdx.x; b < ncols * nb; b += blockDim.x) {
+        for (int b = tg.tid; b < ncols * nb; b += tg.nth) {
             const int col = b / nb;
             const int j = b - col * nb;
             if constexpr (Z0 && S == 0 && R == 3)
@@ -408,7 +413,7 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
                 stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
         }
         __syncthreads();
-        return fft_fixed_stage<T, SIGN, M, F, S + 1, Z0>(dst, src, ncols, tw, twtan);
+        return fft_fixed_stage<T, SIGN, M, F, S + 1, Z0>(tg, dst, src, ncols, tw, twtan);
     }
 }
 
@@ -421,18 +426,18 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(typename V2<T>::t*
 // float64 z transforms are launched only for lengths with a compile-time
 // plan (the host checks tc_fft_fixed_length).
 template <typename T, int SIGN, int F, bool Z0 = false>
-__device__ typename V2<T>::t* fft(typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
+__device__ typename V2<T>::t* fft(const TG tg, typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw,
                                   const double* __restrict__ twtan = nullptr) {
-#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0, Z0>(buf0, buf1, ncols, tw, twtan);
+#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0, Z0>(tg, buf0, buf1, ncols, tw, twtan);
     if constexpr (F == 2) {
-        return fft_stockham<T, SIGN, 2>(buf0, buf1, ncols, pl, tw);
+        return fft_stockham<T, SIGN, 2>(tg, buf0, buf1, ncols, pl, tw);
     } else {
         switch (pl.M) {
             TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
             TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
             TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
-            default: return fft_stockham<T, SIGN, (F == 3 ? 0 : F)>(buf0, buf1, ncols, pl, tw);
+            default: return fft_stockham<T, SIGN, (F == 3 ? 0 : F)>(tg, buf0, buf1, ncols, pl, tw);
         }
     }
 #undef TC_FFT_CASE
@@ -462,7 +467,7 @@ __device__ __forceinline__ void pair_bfly(typename V2<T>::t* src, typename V2<T>
         stockham_bfly<R, SIGN, T>(src, dst, j, nb, Ns, tw + plan_off_f(M, S, F));
 }
 template <typename T, int SIGN, int M1, int M2, int S, bool Z0A = false, int FA = 0>
-__device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V2<T>::t* a1,
+__device__ __forceinline__ void fft_pair_stage(const TG tg, typename V2<T>::t* a0, typename V2<T>::t* a1,
                                                typename V2<T>::t* b0, typename V2<T>::t* b1,
                                                typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                                                const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
@@ -476,7 +481,7 @@ __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V
         constexpr int nb1 = A ? M1 / plan_radix_f(M1, S, FA) : 0;
         constexpr int nb2 = B ? M2 / plan_radix_f(M2, S, 0) : 0;
         const int nA = A ? na * nb1 : 0;
-        for (int b = threadIdx.x; b < nA + nb2; b += blockDim.x) {
+        for (int b = tg.tid; b < nA + nb2; b += tg.nth) {
             if constexpr (A) {
                 if (b < nA) {
                     const int col = b / nb1;
@@ -487,7 +492,7 @@ __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V
             if constexpr (B) pair_bfly<T, SIGN, M2, (B ? S : 0)>(b0, b1, b - nA, tw2, tt2);
         }
         __syncthreads();
-        fft_pair_stage<T, SIGN, M1, M2, S + 1, Z0A, FA>(A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
+        fft_pair_stage<T, SIGN, M1, M2, S + 1, Z0A, FA>(tg, A ? a1 : a0, A ? a0 : a1, B ? b1 : b0, B ? b0 : b1,
                                                         a_res, b_res, na, tw1, tt1, tw2, tt2);
     }
 }
@@ -498,11 +503,11 @@ __device__ __forceinline__ void fft_pair_stage(typename V2<T>::t* a0, typename V
 // p1 and tw1 stay the family-0 plan, used only where a length has no
 // compile-time plan).
 template <typename T, int SIGN, bool FUSE, bool Z0A = false, int FA = 0>
-__device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename V2<T>::t* b0, typename V2<T>::t* b1,
+__device__ void fft_pair(const TG tg, typename V2<T>::t* a0, typename V2<T>::t* a1, typename V2<T>::t* b0, typename V2<T>::t* b1,
                          typename V2<T>::t*& a_res, typename V2<T>::t*& b_res, int na,
                          const FftPlan& p1, const typename V2<T>::t* __restrict__ tw1, const double* __restrict__ tt1,
                          const FftPlan& p2, const typename V2<T>::t* __restrict__ tw2, const double* __restrict__ tt2) {
-#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0, Z0A, FA>(a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
+#define TC_PAIR_CASE(MM) case MM: if (p2.M == MM / 2) { fft_pair_stage<T, SIGN, MM, MM / 2, 0, Z0A, FA>(tg, a0, a1, b0, b1, a_res, b_res, na, tw1, tt1, tw2, tt2); return; } break;
     if constexpr (FUSE) {
         switch (p1.M) {
             TC_PAIR_CASE(24) TC_PAIR_CASE(36) TC_PAIR_CASE(48) TC_PAIR_CASE(72) TC_PAIR_CASE(96)
@@ -512,8 +517,8 @@ __device__ void fft_pair(typename V2<T>::t* a0, typename V2<T>::t* a1, typename 
         }
     }
 #undef TC_PAIR_CASE
-    a_res = fft<T, SIGN, FA, Z0A>(a0, a1, na, p1, tw1, tt1);
-    b_res = fft<T, SIGN, 0>(b0, b1, 1, p2, tw2, tt2);
+    a_res = fft<T, SIGN, FA, Z0A>(tg, a0, a1, na, p1, tw1, tt1);
+    b_res = fft<T, SIGN, 0>(tg, b0, b1, 1, p2, tw2, tt2);
 }
 
 // z twiddles of the plan the kernel runs: pz (family 1) or pz0 (family 0).
@@ -548,18 +553,17 @@ template <> __device__ __forceinline__ const float2* twr<float>(const TcDev& d) 
 // ZF = 0: float64 with the radix-3/4/2 plan pz0 and tangent-form twiddles
 // (compile-time lengths only); ZF = 1: axial lengths 2^a 3^b; ZF = 2:
 // lengths with odd prime factors.
+// Block (bx, r, f): z tile bx + tile0 of radial plane r, field f.
 template <typename T, int ZF>
-__global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict__ f0,
-                                              const double2* __restrict__ f1,
-                                              const double2* __restrict__ f2, int tile0) {
+__device__ __forceinline__ void zinv_body(const TcDev& d, const double2* __restrict__ f0,
+                                          const double2* __restrict__ f1, const double2* __restrict__ f2,
+                                          int tile0, int bx, int r, int f) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     const int ct = d.ztile;
     C* buf1 = buf0 + ct * d.Mz;
-    const int j0 = (blockIdx.x + tile0) * ct;
-    const int r = blockIdx.y;
-    const int f = blockIdx.z;
+    const int j0 = (bx + tile0) * ct;
     const double2* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
@@ -575,12 +579,27 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
         buf0[c * Mz + q] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1, ZF, (ZF == 0)>(buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
+    C* res = fft<T, +1, ZF, (ZF == 0)>(tg_block(), buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx / ct, c = idx - q * ct;
         out[(size_t)q * Nh + j0 + c] = res[c * Mz + q];
     }
+}
+template <typename T, int ZF>
+__global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict__ f0,
+                                              const double2* __restrict__ f1,
+                                              const double2* __restrict__ f2, int tile0) {
+    zinv_body<T, ZF>(d, f0, f1, f2, tile0, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+// Many cases of one shape class (the same Ntheta, Nz, z tile and form) in
+// one launch: grid y runs over the radial planes of every case, ymap[y] =
+// (case, plane); the case's descriptor holds its own fields and tables.
+template <typename T, int ZF>
+__global__ void __launch_bounds__(256) k_zinv_b(const TcDev* __restrict__ ds, const int2* __restrict__ ymap) {
+    const int2 m = ymap[blockIdx.y];
+    const TcDev& d = ds[m.x];
+    zinv_body<T, ZF>(d, d.u, d.v, d.w, 0, blockIdx.x, m.y, blockIdx.z);
 }
 
 // ---- k_rows: theta transforms and products for one (r, q) row --------------
@@ -606,12 +625,15 @@ __global__ void __launch_bounds__(256) k_zinv(TcDev d, const double2* __restrict
 // both); the double-float rows, latency-bound and at a higher register count
 // when fused, run them one after the other.
 template <typename T, int LAYOUT, bool FUSE>
-__global__ void __launch_bounds__(256) k_rows(TcDev d) {
+__device__ __forceinline__ void rows_body(const TcDev& d, const int q, const int r, const TG tg, const int sub) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
     const int H = Mt / 2;
-    C* F1 = reinterpret_cast<C*>(smem_raw);
+    // row group `sub` of the block owns LAYOUT Mt complex values of shared
+    // memory; a group past the last row computes on zeros and stores nothing
+    const bool valid = q < Mz;
+    C* F1 = reinterpret_cast<C*>(smem_raw) + (size_t)sub * LAYOUT * Mt;
     C *F2, *F3, *H1, *H2;
     if constexpr (LAYOUT == 5) {            // [F1 (2 Mt) | H1 | F2 (2 Mt) | H2]
         H1 = F1 + 2 * Mt;
@@ -624,16 +646,17 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         H1 = F3 + Mt;
         H2 = H1 + H;
     }
-    const int q = blockIdx.x, r = blockIdx.y;
     const C* zb = reinterpret_cast<const C*>(d.zbuf);
-    const C* ur = zb + (((size_t)0 * Nr + r) * Mz + q) * Nh;
-    const C* vr = zb + (((size_t)1 * Nr + r) * Mz + q) * Nh;
-    const C* wr = zb + (((size_t)2 * Nr + r) * Mz + q) * Nh;
+    const int qv = valid ? q : 0;
+    const C* ur = zb + (((size_t)0 * Nr + r) * Mz + qv) * Nh;
+    const C* vr = zb + (((size_t)1 * Nr + r) * Mz + qv) * Nh;
+    const C* wr = zb + (((size_t)2 * Nr + r) * Mz + qv) * Nh;
     const C* tr = twr<T>(d);
-    for (int p = threadIdx.x; p < Mt; p += blockDim.x) {
+    for (int p = tg.tid; p < Mt; p += tg.nth) {
         C a;
         a.x = 0; a.y = 0;
-        if (p == 0) {
+        if (!valid) {
+        } else if (p == 0) {
             a.x = ur[0].x; a.y = vr[0].x;
         } else if (p < Nh) {
             C U = ur[p], V = vr[p];
@@ -645,12 +668,12 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         }
         F1[p] = a;
     }
-    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+    for (int k = tg.tid; k < H; k += tg.nth) {
         C xk, xm;
         xk.x = 0; xk.y = 0; xm.x = 0; xm.y = 0;
-        if (k < Nh) { xk = wr[k]; if (k == 0) xk.y = 0; }
+        if (valid && k < Nh) { xk = wr[k]; if (k == 0) xk.y = 0; }
         const int kk = H - k;
-        if (k > 0 && kk < Nh) xm = wr[kk];
+        if (valid && k > 0 && kk < Nh) xm = wr[kk];
         // E = xk + conj(xm), O = (xk - conj(xm)) exp(+2 pi i k/Mt)
         C E, Dd, O, z;
         E.x = xk.x + xm.x; E.y = xk.y - xm.y;
@@ -662,7 +685,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     }
     __syncthreads();
     C *r1, *r2;
-    fft_pair<T, +1, FUSE, true>(F1, F2, H1, H2, r1, r2, 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
+    fft_pair<T, +1, FUSE, true>(tg, F1, F2, H1, H2, r1, r2, 1, d.pt, twt<T>(d), d.twt_tan, d.ph, twh<T>(d), d.twh_tan);
     C* o1 = (r1 == F1) ? F2 : F1;              // free full buffer(s)
     C* o2 = (r2 == H1) ? H2 : H1;              // free half buffer
     C* p2 = (LAYOUT == 5) ? o1 + Mt : F3;      // where uw + i vw goes
@@ -672,7 +695,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     // per output value in the unpacking and two more in k_zfwd.
     constexpr bool PRE = std::is_same<T, double>::value;
     const T s = PRE ? (T)(0.5 * d.fscale) : (T)1;
-    for (int m = threadIdx.x; m < H; m += blockDim.x) {
+    for (int m = tg.tid; m < H; m += tg.nth) {
         const C w2 = r2[m];
         T bb[2];
         for (int e = 0; e < 2; ++e) {
@@ -702,7 +725,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     constexpr int FA = PRE ? 3 : 0;
     const double* tta = PRE ? d.twt3_tan : d.twt_tan;
     C *s1, *s3;
-    fft_pair<T, -1, FUSE, false, FA>(o1, r1, o2, r2, s1, s3, LAYOUT == 5 ? 2 : 1, d.pt, twt<T>(d), tta, d.ph, twh<T>(d), d.twh_tan);
+    fft_pair<T, -1, FUSE, false, FA>(tg, o1, r1, o2, r2, s1, s3, LAYOUT == 5 ? 2 : 1, d.pt, twt<T>(d), tta, d.ph, twh<T>(d), d.twh_tan);
     C* pb = reinterpret_cast<C*>(d.pbuf);
     // unpack two real transforms from one complex transform of length Mt
     auto half = [](T x) -> T {                 // the unpacking's 1/2 (already in s for float64)
@@ -723,7 +746,7 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
         pb[(((size_t)(slot + 1) * Nr + r) * Mz + q) * Nh + j] = x2;
     };
     constexpr int NF = (LAYOUT == 5) ? 2 : 1;   // full columns written now
-    for (int idx = threadIdx.x; idx < (NF + 1) * Nh; idx += blockDim.x) {
+    for (int idx = valid ? tg.tid : (NF + 1) * Nh; idx < (NF + 1) * Nh; idx += tg.nth) {
         const int c = idx / Nh, j = idx - c * Nh;
         if (c < NF) {
             unpack_full(s1 + c * Mt, j, 2 * c);     // uu - vv, uv (and uw, vw)
@@ -742,22 +765,40 @@ __global__ void __launch_bounds__(256) k_rows(TcDev d) {
     }
     if constexpr (LAYOUT == 4) {
         // uw + i vw: its ping-pong partner is the full buffer not holding s1
-        C* s2 = fft<T, -1, FA>(F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), tta);
-        for (int j = threadIdx.x; j < Nh; j += blockDim.x) unpack_full(s2, j, 2);   // uw, vw
+        C* s2 = fft<T, -1, FA>(tg, F3, (s1 == o1) ? r1 : o1, 1, d.pt, twt<T>(d), tta);
+        for (int j = valid ? tg.tid : Nh; j < Nh; j += tg.nth) unpack_full(s2, j, 2);   // uw, vw
     }
+}
+// rpb rows per block (short rows: more rows per block keep the threads of a
+// block busy), blockDim.x / rpb threads per row.
+__device__ __forceinline__ TG row_group(int rpb, int& sub) {
+    const int nth = (int)blockDim.x / rpb;
+    sub = (int)threadIdx.x / nth;
+    return TG{(int)threadIdx.x - sub * nth, nth};
+}
+template <typename T, int LAYOUT, bool FUSE>
+__global__ void __launch_bounds__(256) k_rows(TcDev d, int rpb) {
+    int sub;
+    const TG tg = row_group(rpb, sub);
+    rows_body<T, LAYOUT, FUSE>(d, blockIdx.x * rpb + sub, blockIdx.y, tg, sub);
+}
+template <typename T, int LAYOUT, bool FUSE>
+__global__ void __launch_bounds__(256) k_rows_b(const TcDev* __restrict__ ds, const int2* __restrict__ ymap, int rpb) {
+    const int2 m = ymap[blockIdx.y];
+    int sub;
+    const TG tg = row_group(rpb, sub);
+    rows_body<T, LAYOUT, FUSE>(ds[m.x], blockIdx.x * rpb + sub, m.y, tg, sub);
 }
 
 // ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) (float64: already in pbuf) ----
 template <typename T, int ZF>
-__global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
+__device__ __forceinline__ void zfwd_body(const TcDev& d, int tile0, int bx, int r, int p) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     const int ct = d.ztile;
     C* buf1 = buf0 + ct * d.Mz;
-    const int j0 = (blockIdx.x + tile0) * ct;
-    const int r = blockIdx.y;
-    const int p = blockIdx.z;
+    const int j0 = (bx + tile0) * ct;
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh, Nr = d.Nr;
     const C* in = reinterpret_cast<const C*>(d.pbuf) + ((size_t)p * Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
@@ -767,7 +808,7 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
     __syncthreads();
     // family 3 (float64): the last stage skips outputs M/3 .. 2M/3 - 1, i.e.
     // q = Nz/2 .. Nz - 1, which the truncation below never reads
-    C* res = fft<T, -1, ZF>(buf0, buf1, ct, (ZF == 0 || ZF == 3) ? d.pz0 : d.pz, twz_of<T, ZF>(d),
+    C* res = fft<T, -1, ZF>(tg_block(), buf0, buf1, ct, (ZF == 0 || ZF == 3) ? d.pz0 : d.pz, twz_of<T, ZF>(d),
                             ZF == 3 ? d.twz3_tan : d.twz_tan);
     T scale;
     if constexpr (std::is_same<T, double>::value) scale = 1.0;     // applied in k_rows
@@ -789,6 +830,15 @@ __global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
         outp[(size_t)s * Nh + j0 + c] = val;
     }
 }
+template <typename T, int ZF>
+__global__ void __launch_bounds__(256) k_zfwd(TcDev d, int tile0) {
+    zfwd_body<T, ZF>(d, tile0, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+template <typename T, int ZF>
+__global__ void __launch_bounds__(256) k_zfwd_b(const TcDev* __restrict__ ds, const int2* __restrict__ ymap) {
+    const int2 m = ymap[blockIdx.y];
+    zfwd_body<T, ZF>(ds[m.x], 0, blockIdx.x, m.y, blockIdx.z);
+}
 
 // ---- host launchers --------------------------------------------------------------
 static inline bool z_has_odd_primes(const TcDev& d) {
@@ -805,6 +855,14 @@ static int rows_layout(const TcDev& d) {
     typedef typename V2<T>::t C;
     if (std::is_same<T, dfloat>::value) return 5;
     return 5 * (size_t)d.Mt * sizeof(C) <= 57 * 1024 ? 5 : 4;
+}
+// Theta rows per block: about 384 points per block (one row from Mt = 288 up,
+// up to 8 rows of 48 or fewer points), so that the 256 threads of a block
+// have butterflies to work on in every stage.
+static int rows_per_block(const TcDev& d) {
+    int rpb = 1;
+    while (rpb < 8 && (rpb * 2) * d.Mt <= 384) rpb *= 2;
+    return rpb;
 }
 
 template <typename T>
@@ -825,8 +883,10 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
         else k_zinv<T, 1><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
     } else if (which == 1) {
         constexpr bool fuse = !std::is_same<T, dfloat>::value;
-        if (layout == 5) k_rows<T, 5, fuse><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
-        else k_rows<T, 4, fuse><<<dim3(d.Mz, d.Nr), 256, smr, s>>>(d);
+        const int rpb = rows_per_block(d);
+        const dim3 g((d.Mz + rpb - 1) / rpb, d.Nr);
+        if (layout == 5) k_rows<T, 5, fuse><<<g, 256, rpb * smr, s>>>(d, rpb);
+        else k_rows<T, 4, fuse><<<g, 256, rpb * smr, s>>>(d, rpb);
     } else {
         const dim3 g(ntiles, d.Nr, TC_NPROD);
         if (odd) k_zfwd<T, 2><<<g, 256, smz, s>>>(d, tile0);
@@ -837,6 +897,42 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
     }
 }
 
+
+// One plane kernel for every case of a shape class: d0 is the class's
+// representative descriptor (shapes, z tile, plans), ds the descriptors of
+// all its cases on the device, ymap (case, plane) for each of the nplanes
+// radial planes.  The kernels and launch shapes are those of the single case.
+template <typename T>
+static void plane_kernel_batch_t(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which,
+                                 cudaStream_t s) {
+    typedef typename V2<T>::t C;
+    const int ct = d0.ztile;
+    const size_t smz = 2 * (size_t)ct * d0.Mz * sizeof(C);
+    const int layout = rows_layout<T>(d0);
+    const size_t smr = (size_t)layout * d0.Mt * sizeof(C);
+    const bool odd = z_has_odd_primes(d0);
+    const bool fam0 = d0.zfam0 != 0;
+    const int ntiles = d0.Nh / ct;
+    if (which == 0) {
+        const dim3 g(ntiles, nplanes, 3);
+        if (odd) k_zinv_b<T, 2><<<g, 256, smz, s>>>(ds, ymap);
+        else if (fam0) k_zinv_b<T, 0><<<g, 256, smz, s>>>(ds, ymap);
+        else k_zinv_b<T, 1><<<g, 256, smz, s>>>(ds, ymap);
+    } else if (which == 1) {
+        constexpr bool fuse = !std::is_same<T, dfloat>::value;
+        const int rpb = rows_per_block(d0);
+        const dim3 g((d0.Mz + rpb - 1) / rpb, nplanes);
+        if (layout == 5) k_rows_b<T, 5, fuse><<<g, 256, rpb * smr, s>>>(ds, ymap, rpb);
+        else k_rows_b<T, 4, fuse><<<g, 256, rpb * smr, s>>>(ds, ymap, rpb);
+    } else {
+        const dim3 g(ntiles, nplanes, TC_NPROD);
+        if (odd) k_zfwd_b<T, 2><<<g, 256, smz, s>>>(ds, ymap);
+        else if (fam0) {
+            if constexpr (std::is_same<T, double>::value) k_zfwd_b<T, 3><<<g, 256, smz, s>>>(ds, ymap);
+            else k_zfwd_b<T, 0><<<g, 256, smz, s>>>(ds, ymap);
+        } else k_zfwd_b<T, 1><<<g, 256, smz, s>>>(ds, ymap);
+    }
+}
 
 // Shared-memory opt-in of every plane kernel of one arithmetic type.
 template <typename T>
@@ -852,5 +948,9 @@ static cudaError_t plane_attributes_t() {
     set((const void*)k_zfwd<T, 0>); set((const void*)k_zfwd<T, 1>); set((const void*)k_zfwd<T, 2>);
     if constexpr (std::is_same<T, double>::value) set((const void*)k_zfwd<T, 3>);
     set((const void*)k_rows<T, 5, fuse>); set((const void*)k_rows<T, 4, fuse>);
+    set((const void*)k_zinv_b<T, 0>); set((const void*)k_zinv_b<T, 1>); set((const void*)k_zinv_b<T, 2>);
+    set((const void*)k_zfwd_b<T, 0>); set((const void*)k_zfwd_b<T, 1>); set((const void*)k_zfwd_b<T, 2>);
+    if constexpr (std::is_same<T, double>::value) set((const void*)k_zfwd_b<T, 3>);
+    set((const void*)k_rows_b<T, 5, fuse>); set((const void*)k_rows_b<T, 4, fuse>);
     return e;
 }

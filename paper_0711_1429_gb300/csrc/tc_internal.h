@@ -143,11 +143,23 @@ void tc_launch_plane_phase(const TcDev& d, cudaStream_t s);
 void tc_launch_plane_kernel(const TcDev& d, int which, cudaStream_t s);
 // z kernels (which = 0 or 2) on the z tiles tile0 .. tile0 + ntiles - 1 only
 void tc_launch_plane_kernel_tiles(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles);
+// one plane kernel (which as above) for all cases of a shape class: d0 the
+// class's representative descriptor, ds / ymap on the device (descriptor per
+// case; (case, radial plane) per grid row, nplanes rows)
+void tc_launch_plane_kernel_batch(const TcDev& d0, const TcDev* ds, const int2* ymap, int nplanes, int which,
+                                  cudaStream_t s);
 cudaError_t tc_probe_fma(double* fp64_tflops, double* fp32_tflops);
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s);
 // line phase of the pairs with azimuthal index j0 <= j < j0 + nj (all axial slots)
 void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int j0, int nj);
 void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s);
+// line phase and mean flow of substep k for many cases of one precision form
+// (descriptors ds on the device): the line kernel in nblocks blocks of
+// tc_line_batch_block() threads, bmap[block] = (case, block within the case);
+// the mean flow one block per case, maxNr the largest Nr among them
+void tc_launch_line_batch(int prec, const TcDev* ds, const int2* bmap, int nblocks, int k, cudaStream_t s);
+void tc_launch_mean_batch(int prec, const TcDev* ds, int ncases, int maxNr, int k, cudaStream_t s);
+int tc_line_batch_block();
 void tc_launch_setup_tables(const TcDev& d, cudaStream_t s);
 void tc_launch_init_state(const TcDev& d, cudaStream_t s);
 // zero the (0,0) and Nyquist slots and make the m = 0 column Hermitian

@@ -425,12 +425,11 @@ __device__ __forceinline__ void inner_terms(const CT& pa, const CT& uv, const CT
 }
 
 template <int MODE>
-__device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw) {
+__device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw, const int idx) {
     constexpr bool MIXED = (MODE == 1);
     typedef typename LineTypes<MODE>::T T;
     typedef typename LineTypes<MODE>::CT CT;
-    // thread -> pair among the columns ja .. ja + jw - 1 of every axial slot
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    // thread idx -> pair among the columns ja .. ja + jw - 1 of every axial slot
     if (idx >= d.Nz * jw) return;
     const int pair = (idx / jw) * d.Nh + ja + idx % jw;
     double m, al;
@@ -640,9 +639,21 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw)
 // Kernel variants: a register budget from launch bounds (threads per block,
 // resident blocks per SM), or an explicit register cap.
 template <int MODE, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k, int ja, int jw) { line_body<MODE>(d, k, ja, jw); }
+__global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k, int ja, int jw) {
+    line_body<MODE>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
+}
 template <int MODE, int NREG>
-__global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k, int ja, int jw) { line_body<MODE>(d, k, ja, jw); }
+__global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k, int ja, int jw) {
+    line_body<MODE>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
+}
+// Many cases in one launch: blocks of 128 threads, bmap[block] = (case,
+// block within the case), the case's descriptor from ds.
+template <int MODE>
+__global__ void __launch_bounds__(128, 4) k_line_b(const TcDev* __restrict__ ds, const int2* __restrict__ bmap, int k) {
+    const int2 m = bmap[blockIdx.x];
+    const TcDev& d = ds[m.x];
+    line_body<MODE>(d, k, 0, d.Nh, m.y * blockDim.x + threadIdx.x);
+}
 
 // ---------------------------------------------------------------------------
 // Initial RK memory H_1 = (M + alpha_1 dt L) x for v and eta, and u, w.
@@ -689,7 +700,7 @@ __global__ void __launch_bounds__(128) k_init(TcDev d) {
 // One block: rows are assembled in parallel into shared memory, then two
 // threads run the banded eliminations (U and W) serially.
 template <typename PT>
-__global__ void __launch_bounds__(256) k_mean(TcDev d, int k, int init) {
+__device__ __forceinline__ void mean_body(const TcDev& d, int k, int init) {
     extern __shared__ double sm[];
     const int N = d.Nr;
     double* A = sm;                    // [2][N][5] system rows
@@ -853,6 +864,11 @@ __global__ void __launch_bounds__(256) k_mean(TcDev d, int k, int init) {
         d.w[(size_t)j * d.npairs] = make_double2(x[N + j], 0.0);
     }
 }
+template <typename PT>
+__global__ void __launch_bounds__(256) k_mean(TcDev d, int k, int init) { mean_body<PT>(d, k, init); }
+// one block per case of a shape class
+template <typename PT>
+__global__ void __launch_bounds__(256) k_mean_b(const TcDev* __restrict__ ds, int k) { mean_body<PT>(ds[blockIdx.x], k, 0); }
 
 // ---------------------------------------------------------------------------
 // Diagnostics: strain-rate density for the viscous dissipation.
@@ -1026,12 +1042,32 @@ void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s) {
     else k_mean<double2><<<1, 256, mean_smem(d), s>>>(d, k, 0);
 }
 
+void tc_launch_line_batch(int prec, const TcDev* ds, const int2* bmap, int nblocks, int k, cudaStream_t s) {
+    if (prec == 1) k_line_b<1><<<nblocks, 128, 0, s>>>(ds, bmap, k);
+    else if (prec == 2) k_line_b<2><<<nblocks, 128, 0, s>>>(ds, bmap, k);
+    else k_line_b<0><<<nblocks, 128, 0, s>>>(ds, bmap, k);
+}
+
+int tc_line_batch_block() { return 128; }
+
+void tc_launch_mean_batch(int prec, const TcDev* ds, int ncases, int maxNr, int k, cudaStream_t s) {
+    TcDev dm;
+    dm.Nr = maxNr;
+    if (prec == 1) k_mean_b<float2><<<ncases, 256, mean_smem(dm), s>>>(ds, k);
+    else if (prec == 2) k_mean_b<dcomplex><<<ncases, 256, mean_smem(dm), s>>>(ds, k);
+    else k_mean_b<double2><<<ncases, 256, mean_smem(dm), s>>>(ds, k);
+}
+
 cudaError_t tc_set_line_kernel_attributes() {
     const int lim = 200 * 1024;
     cudaError_t e = cudaFuncSetAttribute((const void*)k_mean<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute((const void*)k_mean<dcomplex>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
+    for (const void* f : {(const void*)k_mean_b<double2>, (const void*)k_mean_b<dcomplex>, (const void*)k_mean_b<float2>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute((const void*)k_mean<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 

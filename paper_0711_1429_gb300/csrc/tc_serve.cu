@@ -1,8 +1,12 @@
 // Many independent Taylor-Couette cases on one GPU.
 //
 // Batch: N cases of any shapes, each with its own resident state and tables,
-// stepped together by one CUDA graph whose branches are the cases' kernel
-// sequences (launched once per step; the branches run concurrently).
+// stepped together by one CUDA graph per step.  Cases of the same form and
+// Fourier grid (any Nr, radius ratio, Re) form a shape class; each
+// plane-phase kernel runs once per class over the radial planes of all of its
+// cases (the classes as concurrent branches), and the line kernel and the
+// mean flow once per precision form over all of its cases, each block
+// reading its case's descriptor.
 //
 // Server: continuous batching.  Requests (case parameters, initial
 // perturbation, number of steps) are queued by tc_server_submit from any host
@@ -15,6 +19,7 @@
 // Each case's arithmetic is the single-case path, so a result does not depend
 // on what else runs.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -35,42 +40,169 @@ using tcx::set_err;
         }                                                                         \
     } while (0)
 
+// Cases of one shape class (the same form, Ntheta and Nz; any Nr, radius
+// ratio, Re, box): their plane kernels, line kernel and mean flow run as one
+// launch each, over the radial planes / pairs / profiles of all of them.
+struct BatchClass {
+    std::vector<int> cases;
+    TcDev d0;                       // representative descriptor (shapes, z tile, plans)
+    TcDev* ds = nullptr;            // device: one descriptor per case
+    int2* ymap = nullptr;           // device: (case, radial plane) per plane-kernel grid row
+    int nplanes = 0, maxNr = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t join = nullptr;
+};
+
+// Cases of one precision form: their line kernel is one launch over the
+// pairs of all of them (cases ordered by decreasing Nr, so that the longest
+// radial lines start first), their mean flows one launch with a block each.
+struct BatchForm {
+    int prec = 0, ncases = 0, nblocks = 0, maxNr = 0;
+    TcDev* ds = nullptr;
+    int2* bmap = nullptr;           // (case, block within the case) per line-kernel block
+    cudaStream_t sl = nullptr, sm = nullptr;
+    cudaEvent_t jl = nullptr, jm = nullptr;
+};
+
 struct tc_batch {
     std::vector<tc_handle*> cases;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> joins;
+    std::vector<BatchClass> classes;
+    std::vector<BatchForm> forms;
     cudaStream_t root = nullptr;
+    bool own_root = true;
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t graph = nullptr;
 };
 
+static void batch_release_classes(tc_batch* b) {
+    for (auto& c : b->classes) {
+        if (c.ds) cudaFree(c.ds);
+        if (c.ymap) cudaFree(c.ymap);
+        if (c.join) cudaEventDestroy(c.join);
+        if (c.stream) cudaStreamDestroy(c.stream);
+    }
+    b->classes.clear();
+    for (auto& f : b->forms) {
+        if (f.ds) cudaFree(f.ds);
+        if (f.bmap) cudaFree(f.bmap);
+        for (cudaEvent_t e : {f.jl, f.jm}) if (e) cudaEventDestroy(e);
+        for (cudaStream_t t : {f.sl, f.sm}) if (t) cudaStreamDestroy(t);
+    }
+    b->forms.clear();
+}
+
 static void batch_free(tc_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    for (auto e : b->joins) cudaEventDestroy(e);
-    for (auto s : b->streams) cudaStreamDestroy(s);
+    batch_release_classes(b);
     if (b->fork) cudaEventDestroy(b->fork);
-    if (b->root) cudaStreamDestroy(b->root);
+    if (b->root && b->own_root) cudaStreamDestroy(b->root);
     for (auto h : b->cases) tc_destroy(h);
     delete b;
 }
 
+// Group the cases into shape classes and upload each class's descriptors
+// and plane map.  A class runs with the z tile its first case was tuned to
+// (launch shapes do not change the arithmetic).
+static int batch_classes(tc_batch* b) {
+    batch_release_classes(b);
+    std::vector<std::array<int, 3>> keys;
+    for (int i = 0; i < (int)b->cases.size(); ++i) {
+        const TcDev& d = b->cases[i]->d;
+        const std::array<int, 3> key = {d.prec, d.Nh, d.Nz};
+        size_t c = std::find(keys.begin(), keys.end(), key) - keys.begin();
+        if (c == keys.size()) {
+            keys.push_back(key);
+            b->classes.emplace_back();
+            b->classes.back().d0 = d;
+        }
+        b->classes[c].cases.push_back(i);
+    }
+    for (auto& c : b->classes) {
+        std::vector<TcDev> ds;
+        std::vector<int2> ym;
+        for (int i = 0; i < (int)c.cases.size(); ++i) {
+            TcDev d = b->cases[c.cases[i]]->d;
+            d.ztile = c.d0.ztile;
+            ds.push_back(d);
+            for (int r = 0; r < d.Nr; ++r) ym.push_back(make_int2(i, r));
+            c.maxNr = std::max(c.maxNr, d.Nr);
+        }
+        c.nplanes = (int)ym.size();
+        CKR(cudaMalloc(&c.ds, ds.size() * sizeof(TcDev)), TC_ERR_CUDA);
+        CKR(cudaMalloc(&c.ymap, ym.size() * sizeof(int2)), TC_ERR_CUDA);
+        CKR(cudaMemcpy(c.ds, ds.data(), ds.size() * sizeof(TcDev), cudaMemcpyHostToDevice), TC_ERR_CUDA);
+        CKR(cudaMemcpy(c.ymap, ym.data(), ym.size() * sizeof(int2), cudaMemcpyHostToDevice), TC_ERR_CUDA);
+        CKR(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), TC_ERR_CUDA);
+        CKR(cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming), TC_ERR_CUDA);
+    }
+    const int bs = tc_line_batch_block();
+    for (int prec : {TC_PREC_FP64, TC_PREC_MIXED, TC_PREC_DF64}) {
+        std::vector<int> idx;
+        for (int i = 0; i < (int)b->cases.size(); ++i)
+            if (b->cases[i]->d.prec == prec) idx.push_back(i);
+        if (idx.empty()) continue;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return b->cases[a]->d.Nr > b->cases[c]->d.Nr; });
+        b->forms.emplace_back();
+        BatchForm& f = b->forms.back();
+        f.prec = prec;
+        f.ncases = (int)idx.size();
+        std::vector<TcDev> ds;
+        std::vector<int2> bm;
+        for (int i = 0; i < f.ncases; ++i) {
+            const TcDev& d = b->cases[idx[i]]->d;
+            ds.push_back(d);
+            f.maxNr = std::max(f.maxNr, d.Nr);
+            for (int q = 0; q < (d.npairs + bs - 1) / bs; ++q) bm.push_back(make_int2(i, q));
+        }
+        f.nblocks = (int)bm.size();
+        CKR(cudaMalloc(&f.ds, ds.size() * sizeof(TcDev)), TC_ERR_CUDA);
+        CKR(cudaMalloc(&f.bmap, bm.size() * sizeof(int2)), TC_ERR_CUDA);
+        CKR(cudaMemcpy(f.ds, ds.data(), ds.size() * sizeof(TcDev), cudaMemcpyHostToDevice), TC_ERR_CUDA);
+        CKR(cudaMemcpy(f.bmap, bm.data(), bm.size() * sizeof(int2), cudaMemcpyHostToDevice), TC_ERR_CUDA);
+        CKR(cudaStreamCreateWithFlags(&f.sl, cudaStreamNonBlocking), TC_ERR_CUDA);
+        CKR(cudaStreamCreateWithFlags(&f.sm, cudaStreamNonBlocking), TC_ERR_CUDA);
+        CKR(cudaEventCreateWithFlags(&f.jl, cudaEventDisableTiming), TC_ERR_CUDA);
+        CKR(cudaEventCreateWithFlags(&f.jm, cudaEventDisableTiming), TC_ERR_CUDA);
+    }
+    return TC_OK;
+}
+
+// One step of every case, per substep: the plane phase of each shape class
+// (z inverse, theta rows, z forward, one launch each over all of the
+// class's cases; the classes as concurrent branches), then the line phase of
+// each precision form (one launch over all of its cases) beside its mean
+// flows (one launch).
 static int batch_graph(tc_batch* b) {
     if (b->graph) return TC_OK;
-    const int n = (int)b->cases.size();
-    for (int i = 0; i < n; ++i) {
-        int rc = tcx::ensure_init(b->cases[i]);
-        if (!rc) rc = tcx::prepare_pipeline(b->cases[i]);
+    for (auto h : b->cases) {
+        int rc = tcx::ensure_init(h);
         if (rc) return rc;
     }
-    CKR(cudaStreamSynchronize(nullptr), TC_ERR_CUDA);
+    CKR(cudaDeviceSynchronize(), TC_ERR_CUDA);
+    int rc = batch_classes(b);
+    if (rc) return rc;
     cudaGraph_t g;
     CKR(cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal), TC_ERR_CUDA);
     CKR(cudaEventRecord(b->fork, b->root), TC_ERR_CUDA);
-    for (int i = 0; i < n; ++i) {
-        CKR(cudaStreamWaitEvent(b->streams[i], b->fork, 0), TC_ERR_CUDA);
-        tcx::launch_step(b->cases[i], b->streams[i]);
-        CKR(cudaEventRecord(b->joins[i], b->streams[i]), TC_ERR_CUDA);
-        CKR(cudaStreamWaitEvent(b->root, b->joins[i], 0), TC_ERR_CUDA);
+    for (int k = 0; k < 3; ++k) {
+        if (k > 0) CKR(cudaEventRecord(b->fork, b->root), TC_ERR_CUDA);
+        for (auto& c : b->classes) {
+            CKR(cudaStreamWaitEvent(c.stream, b->fork, 0), TC_ERR_CUDA);
+            for (int w = 0; w < 3; ++w) tc_launch_plane_kernel_batch(c.d0, c.ds, c.ymap, c.nplanes, w, c.stream);
+            CKR(cudaEventRecord(c.join, c.stream), TC_ERR_CUDA);
+            CKR(cudaStreamWaitEvent(b->root, c.join, 0), TC_ERR_CUDA);
+        }
+        CKR(cudaEventRecord(b->fork, b->root), TC_ERR_CUDA);
+        for (auto& f : b->forms) {
+            CKR(cudaStreamWaitEvent(f.sl, b->fork, 0), TC_ERR_CUDA);
+            CKR(cudaStreamWaitEvent(f.sm, b->fork, 0), TC_ERR_CUDA);
+            tc_launch_line_batch(f.prec, f.ds, f.bmap, f.nblocks, k, f.sl);
+            tc_launch_mean_batch(f.prec, f.ds, f.ncases, f.maxNr, k, f.sm);
+            CKR(cudaEventRecord(f.jl, f.sl), TC_ERR_CUDA);
+            CKR(cudaEventRecord(f.jm, f.sm), TC_ERR_CUDA);
+            CKR(cudaStreamWaitEvent(b->root, f.jl, 0), TC_ERR_CUDA);
+            CKR(cudaStreamWaitEvent(b->root, f.jm, 0), TC_ERR_CUDA);
+        }
     }
     cudaError_t e = cudaStreamEndCapture(b->root, &g);
     if (e != cudaSuccess) { set_err(std::string("batch graph capture: ") + cudaGetErrorString(e)); return TC_ERR_CUDA; }
@@ -285,16 +417,6 @@ tc_batch* tc_batch_create(int ncases, const tc_params* params) {
             return nullptr;
         }
         b->cases.push_back(h);
-        cudaStream_t s;
-        cudaEvent_t e;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            batch_free(b);
-            set_err("tc_batch_create: stream/event creation failed");
-            return nullptr;
-        }
-        b->streams.push_back(s);
-        b->joins.push_back(e);
     }
     if (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
@@ -334,11 +456,25 @@ int tc_batch_set_stream(tc_batch* b, void* stream) {
     if (!b) { set_err("null batch"); return TC_ERR_ARG; }
     // the graph is launched on the root stream; make the caller's stream the root
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
-    if (b->root) cudaStreamDestroy(b->root);
+    if (b->root && b->own_root) cudaStreamDestroy(b->root);
     b->root = nullptr;
-    if (stream) { b->root = (cudaStream_t)stream; return TC_OK; }
+    if (stream) { b->root = (cudaStream_t)stream; b->own_root = false; return TC_OK; }
     CKR(cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking), TC_ERR_CUDA);
+    b->own_root = true;
     return TC_OK;
+}
+
+int tc_batch_launches_per_step(const tc_batch* b) {
+    if (!b) { set_err("null batch"); return TC_ERR_ARG; }
+    std::vector<std::array<int, 3>> keys;
+    for (auto h : b->cases) {
+        const std::array<int, 3> key = {h->d.prec, h->d.Nh, h->d.Nz};
+        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    std::vector<int> precs;
+    for (auto h : b->cases)
+        if (std::find(precs.begin(), precs.end(), h->d.prec) == precs.end()) precs.push_back(h->d.prec);
+    return 3 * (3 * (int)keys.size() + 2 * (int)precs.size());
 }
 
 size_t tc_batch_device_bytes(const tc_batch* b) {

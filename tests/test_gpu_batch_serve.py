@@ -1,4 +1,6 @@
-"""Many cases on one GPU: the batch (one graph, concurrent branches) and the
+"""Many cases on one GPU: the batch (one graph per step; one launch per
+plane kernel and shape class, one line kernel and one mean-flow launch per
+precision form) and the
 server (continuous batching by device budget).  Each case's result must be
 the one the same case gives alone (bit for bit: the arithmetic per case is
 the single-case path and has no order-dependent reductions)."""
@@ -19,6 +21,19 @@ CASES = [  # Nr, Ntheta, Nz, zeta, Re_i, dt, precision, seed
     (17, 16, 64, 0.80, 1200.0, 2e-3, tc.TC_PREC_MIXED, 1002),
     (49, 48, 24, 0.95, 3000.0, 5e-4, tc.TC_PREC_FP64, 1003),
 ]
+
+
+# shape classes of the batch (form, Ntheta, Nz) with several cases each:
+# different Nr, radius ratio, Re and dt share one launch per kernel
+BATCH_CASES = CASES + [
+    (21, 32, 32, 0.85, 900.0, 1e-3, tc.TC_PREC_FP64, 1004),
+    (40, 64, 32, 0.75, 1500.0, 2e-3, tc.TC_PREC_FP64, 1005),
+    (25, 16, 64, 0.90, 700.0, 1e-3, tc.TC_PREC_MIXED, 1006),
+    (30, 32, 32, 0.80, 1000.0, 1e-3, tc.TC_PREC_DF64, 1007),
+    (19, 32, 32, 0.60, 800.0, 1e-3, tc.TC_PREC_DF64, 1008),
+    (45, 32, 32, 0.92, 2500.0, 5e-4, tc.TC_PREC_FP64, 1009),
+]
+N_CLASSES = 5
 
 
 def _params(c, autotune=0):
@@ -47,19 +62,20 @@ def _alone(c, nsteps, autotune=0):
 
 def test_batch_equals_alone_and_autotune_changes_nothing():
     ensure_lib()
-    ref = [_alone(c, 4) for c in CASES]
+    ref = [_alone(c, 4) for c in BATCH_CASES]
     tuned = _alone(CASES[1], 4, autotune=1)
     assert np.array_equal(tuned[0], ref[1][0]) and np.array_equal(tuned[1], ref[1][1])
-    b = tc.tc_batch_create([_params(c, autotune=1) for c in CASES])
+    b = tc.tc_batch_create([_params(c, autotune=1) for c in BATCH_CASES])
     try:
-        for i, c in enumerate(CASES):
+        assert tc.tc_batch_launches_per_step(b) == 3 * (3 * N_CLASSES + 2 * 3)   # 3 precision forms
+        for i, c in enumerate(BATCH_CASES):
             v, e = _ic(c)
             h = tc.tc_batch_case(b, i)
             tc.tc_set_field(h, tc.TC_FIELD_V, v)
             tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
         tc.tc_batch_step(b, 3)
         tc.tc_batch_step(b, 1)
-        for i in range(len(CASES)):
+        for i in range(len(BATCH_CASES)):
             h = tc.tc_batch_case(b, i)
             assert np.array_equal(tc.tc_get_field(h, tc.TC_FIELD_V), ref[i][0]), i
             assert np.array_equal(tc.tc_get_field(h, tc.TC_FIELD_ETA), ref[i][1]), i
