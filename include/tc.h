@@ -293,6 +293,42 @@ int tc_server_drain(tc_server* s, double timeout_s);
 int tc_server_stats(tc_server* s, tc_server_stats_t* out);
 void tc_server_destroy(tc_server* s);
 
+/* ---- one case split across ranks (a transpose form of the paper's
+ * distributed solver, Sec. 3.1; the paper pipelines radial slabs instead) ----
+ *
+ * Each rank holds a handle of the whole case (every array full-size) and is
+ * given a share: radial planes [r0, r1) for the plane phase (transforms and
+ * products, which are independent per plane) and azimuthal columns
+ * [j0, j1) -- every axial slot of those columns -- for the line phase
+ * (Eqs. 6-7 rows and solves, which couple all planes of one pair); the rank
+ * with j0 = 0 also advances the mean flow.  One substep is
+ *   1. exchange: every rank receives u, v, w of the other ranks' columns on
+ *      its planes (written into its own u, v, w arrays there);
+ *   2. tc_split_planes: the plane phase of its planes -> the slab products,
+ *      TC_ARRAY_PROD_SLAB [5][r1-r0][Nz][Ntheta/2];
+ *   3. exchange: every rank receives the slab products of all ranks for its
+ *      columns (written into TC_ARRAY_PROD [5][Nr][Nz][Ntheta/2] there);
+ *   4. tc_split_pairs: the line phase of its columns (and the mean flow).
+ * The exchanges are the caller's (an all-to-all of each rank's collective
+ * library), on the arrays tc_device_array returns; the results equal those
+ * of tc_step bit for bit.  Products are complex128 in the float64 form,
+ * complex64 in the mixed form and pairs of (hi, lo) float pairs in the
+ * double-float form (16 bytes).  The products 0..4 are uu - vv, uv, uw, vw,
+ * ww - vv.  tc_split_planes / tc_split_pairs queue work on the handle's
+ * stream and return without waiting; tc_split_finish waits and reports a
+ * non-finite state (TC_ERR_NONFINITE).  tc_split_set allocates the slab
+ * buffer and may be called between steps only. */
+enum { TC_ARRAY_U = 0, TC_ARRAY_V = 1, TC_ARRAY_W = 2, TC_ARRAY_ETA = 3,
+       TC_ARRAY_PROD = 4, TC_ARRAY_PROD_SLAB = 5 };
+int tc_split_set(tc_handle* h, int r0, int r1, int j0, int j1);
+int tc_split_planes(tc_handle* h);
+int tc_split_pairs(tc_handle* h);
+int tc_split_finish(tc_handle* h);
+/* Device address of one of the handle's resident arrays (NULL for an
+ * unknown selector or a slab buffer not yet allocated); owned by the
+ * handle.  u, v, w, eta: complex128 [Nr][Nz][Ntheta/2]. */
+void* tc_device_array(tc_handle* h, int which);
+
 /* Spectral -> physical transform that allocates nothing (no counterpart in
  * the paper).
  *

@@ -19,6 +19,7 @@ TC_OK, TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_NONFINITE, TC_ERR_SIZE, TC_ERR_TIMEOUT, T
 TC_FIELD_U, TC_FIELD_V, TC_FIELD_W, TC_FIELD_ETA, TC_FIELD_MEAN_U, TC_FIELD_MEAN_W = range(6)
 TC_SPECTRAL, TC_PHYSICAL = 0, 1
 TC_PREC_FP64, TC_PREC_MIXED, TC_PREC_DF64 = 0, 1, 2
+TC_ARRAY_U, TC_ARRAY_V, TC_ARRAY_W, TC_ARRAY_ETA, TC_ARRAY_PROD, TC_ARRAY_PROD_SLAB = range(6)
 TC_NOALLOC_SCRATCH_BYTES = 16 << 20     # size of the fixed array of tc_to_physical_noalloc
 
 
@@ -121,6 +122,13 @@ def lib():
     L.tc_batch_step.argtypes = [vp, i]
     L.tc_batch_set_stream.restype = i
     L.tc_batch_set_stream.argtypes = [vp, vp]
+    for nm in ("tc_split_planes", "tc_split_pairs", "tc_split_finish"):
+        getattr(L, nm).restype = i
+        getattr(L, nm).argtypes = [vp]
+    L.tc_split_set.restype = i
+    L.tc_split_set.argtypes = [vp, i, i, i, i]
+    L.tc_device_array.restype = vp
+    L.tc_device_array.argtypes = [vp, i]
     L.tc_batch_launches_per_step.restype = i
     L.tc_batch_launches_per_step.argtypes = [vp]
     L.tc_batch_device_bytes.restype = sz
@@ -330,6 +338,32 @@ def tc_to_physical_noalloc(Nr, Ntheta, Nz, spectral_dev_ptr, physical_dev_ptr, s
 
 def tc_estimate_device_bytes(params):
     return lib().tc_estimate_device_bytes(ctypes.byref(params))
+
+
+def tc_split_set(h, r0, r1, j0, j1):
+    """This rank's share of a case split across ranks: radial planes [r0, r1)
+    for the plane phase, azimuthal columns [j0, j1) for the line phase."""
+    return _check(lib().tc_split_set(h, r0, r1, j0, j1))
+
+
+def tc_split_planes(h):
+    return _check(lib().tc_split_planes(h))
+
+
+def tc_split_pairs(h):
+    return _check(lib().tc_split_pairs(h))
+
+
+def tc_split_finish(h):
+    return _check(lib().tc_split_finish(h))
+
+
+def tc_device_array(h, which):
+    """Device address (an integer) of one of the handle's resident arrays."""
+    p = lib().tc_device_array(h, which)
+    if not p:
+        raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
+    return p
 
 
 def tc_batch_create(params_list):

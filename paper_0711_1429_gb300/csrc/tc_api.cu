@@ -962,6 +962,77 @@ int tc_advance_substeps(tc_handle* h, int nsub) {
     return check_flags(h);
 }
 
+// ---- one case split across ranks (transpose form) ------------------------
+int tc_split_set(tc_handle* h, int r0, int r1, int j0, int j1) {
+    tcx::Range nvtx_range("tc_split_set");
+    if (!h) { set_err("null handle"); return TC_ERR_ARG; }
+    const TcDev& d = h->d;
+    if (r0 < 0 || r1 > d.Nr || r0 >= r1 || j0 < 0 || j1 > d.Nh || j0 >= j1) {
+        set_err("tc_split_set: need 0 <= r0 < r1 <= Nr and 0 <= j0 < j1 <= Ntheta/2");
+        return TC_ERR_ARG;
+    }
+    if (h->phase != 0) { set_err("tc_split_set: inside a step"); return TC_ERR_ARG; }
+    if (!h->prod_slab || r1 - r0 > h->split_r1 - h->split_r0) {
+        double2* p = nullptr;
+        if (int rc = dalloc(h, p, (size_t)TC_NPROD * (r1 - r0) * d.npairs)) return rc;
+        h->prod_slab = p;
+    }
+    h->split = true;
+    h->split_r0 = r0; h->split_r1 = r1; h->split_j0 = j0; h->split_j1 = j1;
+    return TC_OK;
+}
+
+int tc_split_planes(tc_handle* h) {
+    tcx::Range nvtx_range("tc_split_planes");
+    if (!h || !h->split) { set_err("tc_split_planes: no split set"); return TC_ERR_ARG; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    // the plane kernels on the slab: its planes of u, v, w, the scratch
+    // buffers from their start, the products into the slab buffer
+    TcDev ds = h->d;
+    const size_t off = (size_t)h->split_r0 * ds.npairs;
+    ds.Nr = h->split_r1 - h->split_r0;
+    ds.u += off; ds.v += off; ds.w += off;
+    ds.prod = h->prod_slab;
+    tc_launch_plane_phase(ds, h->stream);
+    CK(cudaGetLastError());
+    return TC_OK;
+}
+
+int tc_split_pairs(tc_handle* h) {
+    tcx::Range nvtx_range("tc_split_pairs");
+    if (!h || !h->split) { set_err("tc_split_pairs: no split set"); return TC_ERR_ARG; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    const int k = h->phase;
+    tc_launch_line_chunk(h->d, k, h->stream, h->split_j0, h->split_j1 - h->split_j0);
+    if (h->split_j0 == 0) tc_launch_mean_phase(h->d, k, h->stream);
+    CK(cudaGetLastError());
+    h->phase = (k + 1) % 3;
+    if (h->phase == 0) { h->t += h->d.dt; h->step += 1; }
+    return TC_OK;
+}
+
+int tc_split_finish(tc_handle* h) {
+    if (!h) { set_err("null handle"); return TC_ERR_ARG; }
+    CK(cudaStreamSynchronize(h->stream));
+    return check_flags(h);
+}
+
+void* tc_device_array(tc_handle* h, int which) {
+    if (!h) { set_err("null handle"); return nullptr; }
+    const TcDev& d = h->d;
+    switch (which) {
+        case TC_ARRAY_U: return d.u;
+        case TC_ARRAY_V: return d.v;
+        case TC_ARRAY_W: return d.w;
+        case TC_ARRAY_ETA: return d.eta;
+        case TC_ARRAY_PROD: return d.prod;
+        case TC_ARRAY_PROD_SLAB: return h->prod_slab;
+        default: set_err("unknown array"); return nullptr;
+    }
+}
+
 int tc_step(tc_handle* h, int nsteps) {
     tcx::Range nvtx_range("tc_step");
     if (!h || nsteps < 0) { set_err("invalid handle or step count"); return TC_ERR_ARG; }

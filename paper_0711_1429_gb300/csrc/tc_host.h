@@ -40,6 +40,12 @@ struct tc_handle {
     bool pipe_ready = false;
     cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t evz[TC_MAX_CHUNKS] = {}, evl[TC_MAX_CHUNKS] = {}, evm = nullptr, evj[4] = {};
+    // this rank's share of a case split across ranks (tc_split_set): radial
+    // planes [r0, r1) of the plane phase, azimuthal columns [j0, j1) of the
+    // line phase, and the products of its planes [TC_NPROD][r1-r0][Nz][Nh]
+    bool split = false;
+    int split_r0 = 0, split_r1 = 0, split_j0 = 0, split_j1 = 0;
+    void* prod_slab = nullptr;
 };
 
 namespace tcx {
