@@ -129,6 +129,10 @@ def lib():
     L.tc_split_set.argtypes = [vp, i, i, i, i]
     L.tc_device_array.restype = vp
     L.tc_device_array.argtypes = [vp, i]
+    L.tc_set_field_async.restype = i
+    L.tc_set_field_async.argtypes = [vp, i, vp, sz]
+    L.tc_get_field_async.restype = i
+    L.tc_get_field_async.argtypes = [vp, i, vp, sz, vp]
     L.tc_batch_launches_per_step.restype = i
     L.tc_batch_launches_per_step.argtypes = [vp]
     L.tc_batch_device_bytes.restype = sz
@@ -338,6 +342,18 @@ def tc_to_physical_noalloc(Nr, Ntheta, Nz, spectral_dev_ptr, physical_dev_ptr, s
 
 def tc_estimate_device_bytes(params):
     return lib().tc_estimate_device_bytes(ctypes.byref(params))
+
+
+def tc_set_field_async(h, which, host_ptr, nbytes):
+    """tc_set_field from a caller-owned (page-locked) host address, without
+    waiting."""
+    return _check(lib().tc_set_field_async(h, which, host_ptr, nbytes))
+
+
+def tc_get_field_async(h, which, host_ptr, nbytes, stream_ptr=None):
+    """Spectral field into a caller-owned host address, ordered after the
+    handle's queued work and run on stream_ptr (None: the handle's stream)."""
+    return _check(lib().tc_get_field_async(h, which, host_ptr, nbytes, stream_ptr))
 
 
 def tc_split_set(h, r0, r1, j0, j1):

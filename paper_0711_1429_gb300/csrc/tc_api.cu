@@ -1169,14 +1169,15 @@ int tc_get_field(tc_handle* h, int which, int space, void* buf, size_t bytes) {
     return TC_OK;
 }
 
-int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
-    tcx::Range nvtx_range("tc_set_field");
+// Shared by tc_set_field and tc_set_field_async: the copy and the Hermitian
+// fix-up are queued on the handle's stream; sync waits for them.
+static int set_field_impl(tc_handle* h, int which, const void* buf, size_t bytes, bool sync) {
     if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
     TcDev& d = h->d;
     if (which == TC_FIELD_MEAN_U || which == TC_FIELD_MEAN_W) {
         if (bytes != (size_t)d.Nr * sizeof(double)) { set_err("mean profile needs Nr float64"); return TC_ERR_SIZE; }
         CK(cudaMemcpyAsync(which == TC_FIELD_MEAN_U ? d.U : d.W, buf, bytes, cudaMemcpyHostToDevice, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+        if (sync) CK(cudaStreamSynchronize(h->stream));
         h->need_init = true;
         h->phase = 0;
         return TC_OK;
@@ -1189,9 +1190,45 @@ int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
     // Hermitian m = 0 column, zero Nyquist slot and (0,0), on the device
     tc_launch_realify(d, dst, h->stream);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(h->stream));
+    if (sync) CK(cudaStreamSynchronize(h->stream));
     h->need_init = true;
     h->phase = 0;
+    return TC_OK;
+}
+
+int tc_set_field(tc_handle* h, int which, const void* buf, size_t bytes) {
+    tcx::Range nvtx_range("tc_set_field");
+    return set_field_impl(h, which, buf, bytes, true);
+}
+
+int tc_set_field_async(tc_handle* h, int which, const void* buf, size_t bytes) {
+    tcx::Range nvtx_range("tc_set_field_async");
+    return set_field_impl(h, which, buf, bytes, false);
+}
+
+int tc_get_field_async(tc_handle* h, int which, void* buf, size_t bytes, void* stream) {
+    tcx::Range nvtx_range("tc_get_field_async");
+    if (!h || !buf) { set_err("null handle or buffer"); return TC_ERR_ARG; }
+    if (which < 0 || which > TC_FIELD_MEAN_W) { set_err("unknown field"); return TC_ERR_ARG; }
+    const size_t need = tc_field_bytes(h, which, TC_SPECTRAL);
+    if (bytes != need) { set_err("buffer size " + std::to_string(bytes) + " != " + std::to_string(need)); return TC_ERR_SIZE; }
+    int rc;
+    if ((rc = ensure_init(h))) return rc;
+    const TcDev& d = h->d;
+    const void* src = which == TC_FIELD_MEAN_U ? (const void*)d.U : which == TC_FIELD_MEAN_W ? (const void*)d.W
+                    : which == TC_FIELD_U ? (const void*)d.u : which == TC_FIELD_V ? (const void*)d.v
+                    : which == TC_FIELD_W ? (const void*)d.w : (const void*)d.eta;
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    if (s != h->stream) {
+        // ordered after everything queued so far on the handle's stream
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+        CK(e);
+    }
+    CK(cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDeviceToHost, s));
     return TC_OK;
 }
 
