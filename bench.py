@@ -460,7 +460,8 @@ def run_gpu(args):
     v, e = initial_perturbation(Nr, Nt, Nz, w["seed"] + rank, w["spectrum"], w["amp"], m0=m0, alpha0=a0, rc=rc)
     peaks = tc.tc_fma_peak(local)
 
-    tq = args.torque_steps if args.precision in ("fp64", "mixed") else 0
+    # the torque run is a one-GPU diagnostic of the headline workload
+    tq = args.torque_steps if args.precision in ("fp64", "mixed") and world == 1 else 0
     h, main = time_form(tc, torch, w, PREC[args.precision], v, e, args, local, dist, measure_clocks=True,
                         torque_steps=tq)
     value = gp * args.steps * world / (main["total_ms"] / 1e3)
@@ -520,7 +521,7 @@ def run_gpu(args):
         ref = main["state"]
         for name in [p for p in ("df64", "mixed", "fp64") if p != args.precision]:
             hf, res = time_form(tc, torch, w, PREC[name], v, e, args, local, dist,
-                                torque_steps=args.torque_steps if name in ("fp64", "mixed") else 0)
+                                torque_steps=args.torque_steps if name in ("fp64", "mixed") and world == 1 else 0)
             tc.tc_destroy(hf)
             if res["series"]:
                 series[name] = res["series"]
