@@ -738,6 +738,7 @@ def served_measure(args, tc, torch, prec_name, local):
     return {"value": st["gridpoint_steps"] / (st["busy_ms"] / 1e3), "unit": UNIT,
             "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2+f64"}[prec_name],
             "requests": len(arrivals), "steps": int(st["steps"]), "rate_per_s": args.serve_rate,
+            "mode": "per case: every admitted case on its own stream, one step in flight each",
             "window_s": args.serve_seconds, "budget_gb": args.budget_gb,
             "peak_active": st["peak_active"], "peak_used_gb": st["peak_used_bytes"] / 1e9,
             "within_budget": st["peak_used_bytes"] <= st["budget_bytes"], "failed": len(bad),

@@ -272,13 +272,23 @@ void tc_batch_destroy(tc_batch* b);
  * copied at submission, number of steps, optional caller-owned host buffers
  * that receive the final v and eta); a worker thread admits queued requests
  * while the estimated device bytes of the admitted cases stay within
- * budget_bytes and at most max_active run, steps every admitted case on its
- * own stream with one step in flight (cases overlap on the device), and on
- * completion writes the outputs, frees the case and admits more.  Requests
- * that alone exceed the budget are refused with TC_ERR_SIZE.  Thread-safe:
- * submit / poll / drain / stats may be called from any host thread.
- * tc_server_destroy drops queued requests and stops running ones after
- * their current step. */
+ * budget_bytes and at most max_active run, steps the admitted cases, and on
+ * completion writes the outputs, frees the case and admits more.  Modes:
+ *   TC_SERVE_PER_CASE (tc_server_create): every case on its own stream with
+ *     its own step graph and one step in flight, relaunched as soon as it
+ *     completes, so each case's step latency is its own.
+ *   TC_SERVE_GROUPED: all admitted cases advance together, one step per
+ *     graph launch of the batch's grouped kernels (one launch per plane
+ *     kernel and shape class, one line-kernel and one mean-flow launch per
+ *     precision form); the graph is captured again whenever the set of cases
+ *     changes, which happens between steps only.  Every case's per-step
+ *     latency is that of the group step.
+ * Results equal those of the same case stepped alone in either mode.
+ * Requests that alone exceed the budget are refused with TC_ERR_SIZE.
+ * Thread-safe: submit / poll / drain / stats may be called from any host
+ * thread.  tc_server_destroy drops queued requests and stops running ones
+ * after their current step. */
+enum { TC_SERVE_PER_CASE = 0, TC_SERVE_GROUPED = 1 };
 typedef struct tc_server tc_server;
 typedef struct {
     long long id;           /* from tc_server_submit */
@@ -298,6 +308,7 @@ typedef struct {
     double step_ms_p50, step_ms_p99;   /* over every step of finished cases */
 } tc_server_stats_t;
 tc_server* tc_server_create(size_t budget_bytes, int max_active, int device);
+tc_server* tc_server_create_ex(size_t budget_bytes, int max_active, int device, int mode);
 int tc_server_submit(tc_server* s, const tc_params* params, const void* v0, const void* eta0,
                      int nsteps, void* out_v, void* out_eta, long long* id);
 int tc_server_poll(tc_server* s, tc_result* out, int max_results, int* count);

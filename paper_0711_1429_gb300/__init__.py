@@ -20,6 +20,7 @@ TC_FIELD_U, TC_FIELD_V, TC_FIELD_W, TC_FIELD_ETA, TC_FIELD_MEAN_U, TC_FIELD_MEAN
 TC_SPECTRAL, TC_PHYSICAL = 0, 1
 TC_PREC_FP64, TC_PREC_MIXED, TC_PREC_DF64 = 0, 1, 2
 TC_ARRAY_U, TC_ARRAY_V, TC_ARRAY_W, TC_ARRAY_ETA, TC_ARRAY_PROD, TC_ARRAY_PROD_SLAB = range(6)
+TC_SERVE_PER_CASE, TC_SERVE_GROUPED = 0, 1
 TC_NOALLOC_SCRATCH_BYTES = 16 << 20     # size of the fixed array of tc_to_physical_noalloc
 
 
@@ -141,6 +142,8 @@ def lib():
     L.tc_batch_destroy.argtypes = [vp]
     L.tc_server_create.restype = vp
     L.tc_server_create.argtypes = [sz, i, i]
+    L.tc_server_create_ex.restype = vp
+    L.tc_server_create_ex.argtypes = [sz, i, i, i]
     L.tc_server_submit.restype = i
     L.tc_server_submit.argtypes = [vp, ctypes.POINTER(tc_params), vp, vp, i, vp, vp,
                                    ctypes.POINTER(ctypes.c_longlong)]
@@ -422,8 +425,11 @@ def tc_batch_destroy(b):
         lib().tc_batch_destroy(b)
 
 
-def tc_server_create(budget_bytes, max_active=64, device=-1):
-    s = lib().tc_server_create(budget_bytes, max_active, device)
+def tc_server_create(budget_bytes, max_active=64, device=-1, mode=None):
+    """Server of independent cases within a device budget; mode
+    TC_SERVE_PER_CASE (default: each case on its own stream) or
+    TC_SERVE_GROUPED (all admitted cases step together in grouped launches)."""
+    s = lib().tc_server_create_ex(budget_bytes, max_active, device, TC_SERVE_PER_CASE if mode is None else mode)
     if not s:
         raise TcError(TC_ERR_ARG, lib().tc_last_error().decode())
     return s

@@ -11,10 +11,12 @@
 // Server: continuous batching.  Requests (case parameters, initial
 // perturbation, number of steps) are queued by tc_server_submit from any host
 // thread; a worker thread admits them while the estimated device bytes of the
-// admitted cases stay within the budget, gives each its own stream, and keeps
-// one step in flight per case, relaunching each case as soon as its previous
-// step completes, so requests that arrive while others run overlap with them
-// on the device.  A finished case is read back (statistics, optional final
+// admitted cases stay within the budget.  Per-case mode (the default): each
+// case has its own stream and one step in flight, relaunched as soon as its
+// previous step completes.  Grouped mode: every admitted case advances by one
+// step in one graph launch of the batch's grouped kernels, and between steps
+// finished cases leave and new ones join.  Either way requests
+// that arrive while others run overlap with them on the device.  A finished case is read back (statistics, optional final
 // v and eta into caller buffers) and freed, which admits waiting requests.
 // Each case's arithmetic is the single-case path, so a result does not depend
 // on what else runs.
@@ -64,7 +66,10 @@ struct BatchForm {
     cudaEvent_t jl = nullptr, jm = nullptr;
 };
 
-struct tc_batch {
+// A set of cases stepped together: their shape classes and precision forms,
+// and the captured graph of one step of all of them (launched on root).
+// Used by the batch, and by the server in its grouped mode.
+struct Group {
     std::vector<tc_handle*> cases;
     std::vector<BatchClass> classes;
     std::vector<BatchForm> forms;
@@ -74,7 +79,9 @@ struct tc_batch {
     cudaGraphExec_t graph = nullptr;
 };
 
-static void batch_release_classes(tc_batch* b) {
+struct tc_batch : Group {};
+
+static void batch_release_classes(Group* b) {
     for (auto& c : b->classes) {
         if (c.ds) cudaFree(c.ds);
         if (c.ymap) cudaFree(c.ymap);
@@ -103,7 +110,7 @@ static void batch_free(tc_batch* b) {
 // Group the cases into shape classes and upload each class's descriptors
 // and plane map.  A class runs with the z tile its first case was tuned to
 // (launch shapes do not change the arithmetic).
-static int batch_classes(tc_batch* b) {
+static int batch_classes(Group* b) {
     batch_release_classes(b);
     std::vector<std::array<int, 3>> keys;
     for (int i = 0; i < (int)b->cases.size(); ++i) {
@@ -172,7 +179,7 @@ static int batch_classes(tc_batch* b) {
 // class's cases; the classes as concurrent branches), then the line phase of
 // each precision form (one launch over all of its cases) beside its mean
 // flows (one launch).
-static int batch_graph(tc_batch* b) {
+static int batch_graph(Group* b) {
     if (b->graph) return TC_OK;
     for (auto h : b->cases) {
         int rc = tcx::ensure_init(h);
@@ -266,6 +273,8 @@ struct tc_server {
     std::thread worker;
     bool stop = false;
     std::string worker_error;
+    int mode = TC_SERVE_PER_CASE;
+    cudaStream_t gstream = nullptr;   // grouped mode: the stream of every admitted case
 };
 
 namespace {
@@ -310,14 +319,19 @@ Active* admit(tc_server* S, Request&& rq) {
     a->t_start = now_ms();
     a->h = tc_create_ex(&a->rq.p);
     int rc = a->h ? TC_OK : TC_ERR_CUDA;
-    if (!rc && cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking) != cudaSuccess) rc = TC_ERR_CUDA;
-    if (!rc && (cudaEventCreate(&a->ev0) != cudaSuccess || cudaEventCreate(&a->ev1) != cudaSuccess)) rc = TC_ERR_CUDA;
-    if (!rc) rc = tc_set_stream(a->h, a->s);
+    const bool grouped = S->mode == TC_SERVE_GROUPED;
+    if (grouped) {
+        if (!rc) rc = tc_set_stream(a->h, S->gstream);
+    } else {
+        if (!rc && cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking) != cudaSuccess) rc = TC_ERR_CUDA;
+        if (!rc && (cudaEventCreate(&a->ev0) != cudaSuccess || cudaEventCreate(&a->ev1) != cudaSuccess)) rc = TC_ERR_CUDA;
+        if (!rc) rc = tc_set_stream(a->h, a->s);
+    }
     const size_t nb = (size_t)a->rq.p.Nr * a->rq.p.Nz * (a->rq.p.Ntheta / 2) * sizeof(double2);
     if (!rc && !a->rq.v0.empty()) rc = tc_set_field(a->h, TC_FIELD_V, a->rq.v0.data(), nb);
     if (!rc && !a->rq.e0.empty()) rc = tc_set_field(a->h, TC_FIELD_ETA, a->rq.e0.data(), nb);
     if (!rc) rc = tcx::ensure_init(a->h);
-    if (!rc) rc = tcx::ensure_graph(a->h);
+    if (!rc && !grouped) rc = tcx::ensure_graph(a->h);
     a->rq.v0.clear(); a->rq.v0.shrink_to_fit();
     a->rq.e0.clear(); a->rq.e0.shrink_to_fit();
     if (rc) { finish(S, a, rc); return nullptr; }
@@ -331,10 +345,108 @@ void launch_one(Active* a) {
     a->in_flight = true;
 }
 
+// Grouped mode: every admitted case steps in one graph launch per step (the
+// batch's grouped kernels over the current set of cases, captured again
+// whenever the set changes); between steps, finished cases leave and queued
+// requests are admitted.
+void worker_grouped(tc_server* S) {
+    Group G;
+    G.own_root = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&G.root, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->worker_error = "stream/event creation failed in the server worker";
+        return;
+    }
+    S->gstream = G.root;
+    bool dirty = true;
+    for (;;) {
+        std::vector<Request> to_admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            while (!S->queue.empty() && (int)(S->active.size() + to_admit.size()) < S->max_active &&
+                   S->used + S->queue.front().need <= S->budget) {
+                S->used += S->queue.front().need;
+                S->peak_used = std::max(S->peak_used, S->used);
+                to_admit.push_back(std::move(S->queue.front()));
+                S->queue.pop_front();
+            }
+            if (S->stop && S->queue.empty() && S->active.empty() && to_admit.empty()) break;
+            if (S->active.empty() && to_admit.empty()) {
+                S->cv.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
+            }
+        }
+        for (auto& rq : to_admit) {
+            Active* a = admit(S, std::move(rq));
+            if (a) {
+                if (S->busy_start < 0) S->busy_start = a->t_start;
+                S->active.push_back(a);
+                dirty = true;
+            }
+        }
+        S->peak_active = std::max(S->peak_active, (int)S->active.size());
+        if (S->active.empty()) continue;
+        int rc = TC_OK;
+        if (dirty) {
+            if (G.graph) { cudaGraphExecDestroy(G.graph); G.graph = nullptr; }
+            batch_release_classes(&G);
+            G.cases.clear();
+            for (Active* a : S->active) G.cases.push_back(a->h);
+            rc = batch_graph(&G);
+            dirty = false;
+        }
+        float ms = 0;
+        if (!rc) {
+            cudaEventRecord(e0, G.root);
+            cudaGraphLaunch(G.graph, G.root);
+            cudaEventRecord(e1, G.root);
+            rc = cudaEventSynchronize(e1) == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        bool stopping;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            stopping = S->stop;
+        }
+        for (size_t i = 0; i < S->active.size();) {
+            Active* a = S->active[i];
+            int st = rc;
+            if (!rc) {
+                a->lat.push_back(ms);
+                a->done++;
+                a->h->t += a->h->d.dt;
+                a->h->step += 1;
+                if (a->done >= a->rq.nsteps || stopping) st = tcx::check_flags(a->h);
+            }
+            if (st != TC_OK || a->done >= a->rq.nsteps || stopping) {
+                S->active.erase(S->active.begin() + i);
+                finish(S, a, st);
+                dirty = true;
+                continue;
+            }
+            ++i;
+        }
+    }
+    if (G.graph) cudaGraphExecDestroy(G.graph);
+    G.graph = nullptr;
+    batch_release_classes(&G);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(G.fork);
+    cudaStreamDestroy(G.root);
+}
+
 void worker_main(tc_server* S) {
     if (cudaSetDevice(S->device) != cudaSuccess) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->worker_error = "cudaSetDevice failed in the server worker";
+        return;
+    }
+    if (S->mode == TC_SERVE_GROUPED) {
+        worker_grouped(S);
         return;
     }
     for (;;) {
@@ -490,10 +602,16 @@ void tc_batch_destroy(tc_batch* b) {
 }
 
 tc_server* tc_server_create(size_t budget_bytes, int max_active, int device) {
+    return tc_server_create_ex(budget_bytes, max_active, device, TC_SERVE_PER_CASE);
+}
+
+tc_server* tc_server_create_ex(size_t budget_bytes, int max_active, int device, int mode) {
     if (budget_bytes == 0 || max_active < 1) { set_err("tc_server_create: budget and max_active must be positive"); return nullptr; }
+    if (mode != TC_SERVE_GROUPED && mode != TC_SERVE_PER_CASE) { set_err("tc_server_create: unknown mode"); return nullptr; }
     tc_server* S = new tc_server();
     S->budget = budget_bytes;
     S->max_active = max_active;
+    S->mode = mode;
     if (device < 0) {
         if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; set_err("cudaGetDevice failed"); return nullptr; }
     } else {

@@ -85,14 +85,15 @@ def test_batch_equals_alone_and_autotune_changes_nothing():
         tc.tc_batch_destroy(b)
 
 
-def test_server_results_equal_alone_within_budget():
+@pytest.mark.parametrize("mode", [tc.TC_SERVE_GROUPED, tc.TC_SERVE_PER_CASE])
+def test_server_results_equal_alone_within_budget(mode):
     ensure_lib()
     steps = [6, 11, 4, 9, 7, 5]
     cases = [CASES[i % len(CASES)] for i in range(len(steps))]
     ref = [_alone(c, n) for c, n in zip(cases, steps)]
     need = sorted(tc.tc_estimate_device_bytes(_params(c)) for c in cases)
     budget = need[-1] + need[-2] + 1          # at most two large cases at a time
-    s = tc.tc_server_create(budget, max_active=8)
+    s = tc.tc_server_create(budget, max_active=8, mode=mode)
     outs = []
     try:
         ids = []
