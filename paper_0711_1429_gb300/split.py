@@ -28,7 +28,7 @@ torch.distributed.all_to_all_single; `exchange_in_process` stands in for it
 when all shares live in one process).
 
 The compute of a share is given as two callables, planes() and pairs(k);
-`LibtcShare` binds them to the libtc calls tc_split_planes / tc_split_pairs
+`libtc_share` binds them to the libtc calls tc_split_planes / tc_split_pairs
 of a handle whose resident arrays the tensors view.
 """
 import torch
@@ -187,7 +187,7 @@ def device_tensor(ptr, shape):
     return torch.as_tensor(_CudaArray(ptr, shape), device="cuda")
 
 
-def LibtcShare(h, plan, rank, precision):
+def libtc_share(h, plan, rank, precision):
     """The share of rank `rank` on a libtc handle h of the whole case (any
     precision form; the handle's launch stream must be torch's current
     stream, so that the copies of the exchanges and the kernels stay in

@@ -44,7 +44,7 @@ def test_split_on_one_gpu_equals_tc_step(world, prec):
     try:
         tc.tc_step(ref, STEPS)
         plan = sp.SplitPlan(Nr, Nt, Nz, world)
-        shares = [sp.LibtcShare(h, plan, r, prec) for r, h in enumerate(hs)]
+        shares = [sp.libtc_share(h, plan, r, prec) for r, h in enumerate(hs)]
         for _ in range(STEPS):
             sp.step_in_process(shares)
         for h in hs:
