@@ -562,12 +562,13 @@ __device__ __forceinline__ void zinv_body(const TcDev& d, const double2* __restr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     const int ct = d.ztile;
+    const int lct = __ffs(ct) - 1;          // the z tile is 1, 2, 4 or 8 columns
     C* buf1 = buf0 + ct * d.Mz;
     const int j0 = (bx + tile0) * ct;
     const double2* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
-        const int q = idx / ct, c = idx - q * ct;
+        const int q = idx >> lct, c = idx & (ct - 1);
         int s = -1;
         if (q < Nz / 2) s = q;
         else if (q > Mz - Nz / 2) s = Nz - (Mz - q);
@@ -582,7 +583,7 @@ __device__ __forceinline__ void zinv_body(const TcDev& d, const double2* __restr
     C* res = fft<T, +1, ZF, (ZF == 0)>(tg_block(), buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
-        const int q = idx / ct, c = idx - q * ct;
+        const int q = idx >> lct, c = idx & (ct - 1);
         out[(size_t)q * Nh + j0 + c] = res[c * Mz + q];
     }
 }
@@ -797,12 +798,13 @@ __device__ __forceinline__ void zfwd_body(const TcDev& d, int tile0, int bx, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     const int ct = d.ztile;
+    const int lct = __ffs(ct) - 1;          // the z tile is 1, 2, 4 or 8 columns
     C* buf1 = buf0 + ct * d.Mz;
     const int j0 = (bx + tile0) * ct;
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh, Nr = d.Nr;
     const C* in = reinterpret_cast<const C*>(d.pbuf) + ((size_t)p * Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
-        const int q = idx / ct, c = idx - q * ct;
+        const int q = idx >> lct, c = idx & (ct - 1);
         buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
@@ -819,7 +821,7 @@ __device__ __forceinline__ void zfwd_body(const TcDev& d, int tile0, int bx, int
     typedef typename std::conditional<std::is_same<T, double>::value, double2, C>::type PO;
     PO* outp = reinterpret_cast<PO*>(d.prod) + ((size_t)p * Nr + r) * Nz * Nh;
     for (int idx = threadIdx.x; idx < ct * Nz; idx += blockDim.x) {
-        const int s = idx / ct, c = idx - s * ct;
+        const int s = idx >> lct, c = idx & (ct - 1);
         C val; val.x = 0; val.y = 0;
         if (s != Nz / 2) {
             const int n = s < Nz / 2 ? s : s - Nz;
