@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--workload", default="tc-257x512x512")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
