@@ -202,7 +202,9 @@ int tc_set_stream(tc_handle* h, void* cuda_stream);
  *          dividing Ntheta/2 (0 keeps the current value);
  *   line_variant: line-kernel launch shape, 64, 128 or 256 threads per
  *          block, 1003 / 1004 (128 threads, budget for 3 / 4 blocks per
- *          SM) or 2007 (64 threads, 144 registers); 0 keeps the current;
+ *          SM), 2007 (64 threads, 144 registers) or 3001 (64 threads per 32
+ *          pairs: one warp advances v, the other eta, for short line phases
+ *          of few pairs); 0 keeps the current;
  *   chunks: column groups of the step graph, in which the z transforms of
  *          one group overlap the line kernel of another: 1 (no overlap), 2,
  *          4 or 8, used when it divides the number of z tiles (0 keeps the

@@ -289,7 +289,7 @@ def tc_load_state(h, image):
     return _check(lib().tc_load_state(h, buf, len(image)))
 
 
-LINE_VARIANTS = (64, 128, 256, 1003, 1004, 2007)
+LINE_VARIANTS = (64, 128, 256, 1003, 1004, 2007, 3001)
 
 
 def tc_set_tiles(h, ztile=0, line_variant=0, chunks=0):

@@ -369,7 +369,7 @@ int autotune(tc_handle* h) {
     d.ztile = best_t;
     best = 1e30f;
     int best_b = d.line_block;
-    for (int bs : {64, 128, 256, 1003, 1004, 2007}) {
+    for (int bs : {64, 128, 256, 1003, 1004, 2007, 3001}) {
         d.line_block = bs;
         const float ms = timed([&] { tc_launch_line_phase(d, 0, h->stream); });
         if (ms < best) { best = ms; best_b = bs; }
@@ -863,8 +863,8 @@ int tc_set_tiles(tc_handle* h, int ztile, int line_variant, int chunks) {
         }
     }
     if (line_variant != 0 && line_variant != 64 && line_variant != 128 && line_variant != 256 &&
-        line_variant != 1003 && line_variant != 1004 && line_variant != 2007) {
-        set_err("line_variant must be 64, 128, 256, 1003, 1004 or 2007");
+        line_variant != 1003 && line_variant != 1004 && line_variant != 2007 && line_variant != 3001) {
+        set_err("line_variant must be 64, 128, 256, 1003, 1004, 2007 or 3001");
         return TC_ERR_ARG;
     }
     if (chunks != 0 && chunks != 1 && chunks != 2 && chunks != 4 && chunks != 8) {

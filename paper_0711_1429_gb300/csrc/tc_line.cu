@@ -424,17 +424,24 @@ __device__ __forceinline__ void inner_terms(const CT& pa, const CT& uv, const CT
     be = tadd(be, timag((T)2 * nut * mt * ri2, U));
 }
 
-template <int MODE>
-__device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw, const int idx) {
+// The sweeps of one pair (ROLE 0: v and eta; 1: v only; 2: eta only, for the
+// kernel in which one thread advances v and another eta of the same pair);
+// returns false for a thread without a pair to evolve.  The arithmetic of
+// each field is the same in every role.
+template <int MODE, int ROLE>
+__device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int jw, const int idx, int& pair_out,
+                                            double& m_out, double& al_out, long long& partner_out) {
     constexpr bool MIXED = (MODE == 1);
+    constexpr bool DV = ROLE != 2, DE = ROLE != 1;
     typedef typename LineTypes<MODE>::T T;
     typedef typename LineTypes<MODE>::CT CT;
     // thread idx -> pair among the columns ja .. ja + jw - 1 of every axial slot
-    if (idx >= d.Nz * jw) return;
+    if (idx >= d.Nz * jw) return false;
     const int pair = (idx / jw) * d.Nh + ja + idx % jw;
     double m, al;
     long long partner;
-    if (!pair_info(d, pair, m, al, partner)) return;
+    if (!pair_info(d, pair, m, al, partner)) return false;
+    pair_out = pair; m_out = m; al_out = al; partner_out = partner;
     const int N = d.Nr;
     const size_t P = d.npairs;
     const CT* prod = reinterpret_cast<const CT*>(d.prod);
@@ -523,8 +530,8 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw,
 
     for (int i = 0; i < N; ++i) {
         for (int s = 0; s < 4; ++s) {
-            Av[s] = Av[s + 1]; Bv[s] = Bv[s + 1]; Cv[s] = Cv[s + 1]; Ae[s] = Ae[s + 1]; Be[s] = Be[s + 1];
-            Cp[s] = Cp[s + 1];
+            if constexpr (DV) { Av[s] = Av[s + 1]; Bv[s] = Bv[s + 1]; Cv[s] = Cv[s + 1]; Cp[s] = Cp[s + 1]; }
+            if constexpr (DE) { Ae[s] = Ae[s + 1]; Be[s] = Be[s + 1]; }
         }
         {
             const size_t o = (size_t)i * P + pair;
@@ -538,42 +545,56 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw,
             else { ri = d.rinv[i]; c = d.tab_c[o]; c1d = d.tab_c1[o]; c1 = c1d; }
             CT a, b, cc, ae, be;
             inner_terms(pa, uv, uw, vw, pb, U, V, W, ri, c, c1, mt, at, nut, a, b, cc, ae, be);
-            if constexpr (MODE == 1) {
-                // phi = i alpha u + (i m/r) w, times c', in double-float
-                const dcomplex phi = dc_i(dc_fma(dc_scale(alD, dc_bits(Ud)), mD * rinvx[i], dc_bits(Wd)));
-                Cp[4] = dc_scale(as_df(d.tab_c1x[o]), phi);
-            } else if constexpr (MODE == 2) {
-                const CT phi = tadd(timag(at, U), timag(mt * ri, W));
-                cc = taxpy(cc, (T)(-3.0 * nu) * c1, phi);
-            } else {
-                const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
-                cc = caxpy(cc, -3.0 * nu * c1d, phi);
+            if constexpr (DV) {
+                if constexpr (MODE == 1) {
+                    // phi = i alpha u + (i m/r) w, times c', in double-float
+                    const dcomplex phi = dc_i(dc_fma(dc_scale(alD, dc_bits(Ud)), mD * rinvx[i], dc_bits(Wd)));
+                    Cp[4] = dc_scale(as_df(d.tab_c1x[o]), phi);
+                } else if constexpr (MODE == 2) {
+                    const CT phi = tadd(timag(at, U), timag(mt * ri, W));
+                    cc = taxpy(cc, (T)(-3.0 * nu) * c1, phi);
+                } else {
+                    const double2 phi = cadd(cimag(al, Ud), cimag(m * d.rinv[i], Wd));
+                    cc = caxpy(cc, -3.0 * nu * c1d, phi);
+                }
+                Av[4] = a; Bv[4] = b; Cv[4] = cc;
             }
-            Av[4] = a; Bv[4] = b; Cv[4] = cc;
-            Ae[4] = ae; Be[4] = be;
+            if constexpr (DE) { Ae[4] = ae; Be[4] = be; }
         }
         if (i < 4) continue;
         const int j = i - 2;
         if (i == 4) {
-            re_row1 = rhs_e(1, erow(1));
-            const double2 rv2 = rhs_v(2, vrow(2));
-            const double2 re2 = rhs_e(2, erow(2));
-            fwd_v(1, cscale(-fv, rv2));
-            fwd_v(2, rv2);
-            fwd_e(1, caxpy(re_row1, -fe, re2));
-            fwd_e(2, re2);
-            rv_prev = rv2; re_prev = re2;
+            if constexpr (DE) re_row1 = rhs_e(1, erow(1));
+            if constexpr (DV) {
+                const double2 rv2 = rhs_v(2, vrow(2));
+                fwd_v(1, cscale(-fv, rv2));
+                fwd_v(2, rv2);
+                rv_prev = rv2;
+            }
+            if constexpr (DE) {
+                const double2 re2 = rhs_e(2, erow(2));
+                fwd_e(1, caxpy(re_row1, -fe, re2));
+                fwd_e(2, re2);
+                re_prev = re2;
+            }
         } else if (j <= N - 3) {
-            const double2 rv = rhs_v(j, vrow(j));
-            const double2 re = rhs_e(j, erow(j));
-            fwd_v(j, rv);
-            fwd_e(j, re);
-            rv_prev = rv; re_prev = re;
+            if constexpr (DV) {
+                const double2 rv = rhs_v(j, vrow(j));
+                fwd_v(j, rv);
+                rv_prev = rv;
+            }
+            if constexpr (DE) {
+                const double2 re = rhs_e(j, erow(j));
+                fwd_e(j, re);
+                re_prev = re;
+            }
         }
         if (i == N - 1) {
-            fwd_v(N - 2, cscale(-gv, rv_prev));
-            const double2 reN = rhs_e(N - 2, erow(N - 2));
-            fwd_e(N - 2, caxpy(reN, -ge, re_prev));
+            if constexpr (DV) fwd_v(N - 2, cscale(-gv, rv_prev));
+            if constexpr (DE) {
+                const double2 reN = rhs_e(N - 2, erow(N - 2));
+                fwd_e(N - 2, caxpy(reN, -ge, re_prev));
+            }
         }
     }
 
@@ -584,11 +605,13 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw,
     bool bad = false;
     const double k2N = al * al + m * m * d.rinv[N - 1] * d.rinv[N - 1];
     xw[0] = cz(); ew[0] = cz(); k2w[0] = k2N;
-    d.v[(size_t)(N - 1) * P + pair] = cz();
-    d.eta[(size_t)(N - 1) * P + pair] = cz();
+    if constexpr (DV) d.v[(size_t)(N - 1) * P + pair] = cz();
+    if constexpr (DE) d.eta[(size_t)(N - 1) * P + pair] = cz();
     const double hdtnu = hdt * nu;
     auto h_update = [&](int jr, bool do_v, bool do_e) {
         const size_t o = (size_t)jr * P + pair;
+        do_v = do_v && DV;
+        do_e = do_e && DE;
         if (do_v) {
             double2 acc = cz();
             for (int s = 0; s < 5; ++s) acc = caxpy(acc, TAB(d.tab_lv, 0, jr, s), xw[s]);
@@ -607,21 +630,28 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw,
         k2w[0] = al * al + m * m * ri * ri;
         if (i >= 1) {
             const size_t o = (size_t)i * P + pair;
-            const double2 yv = d.v[o], ye = d.eta[o];
-            const double2 xv = cscale(TAB(d.tab_luv, k, i, 2),
-                                      caxpy(caxpy(yv, -TAB(d.tab_luv, k, i, 3), xw[1]), -TAB(d.tab_luv, k, i, 4), xw[2]));
-            const double2 xe = cscale(TAB(d.tab_lue, k, i, 2),
-                                      caxpy(caxpy(ye, -TAB(d.tab_lue, k, i, 3), ew[1]), -TAB(d.tab_lue, k, i, 4), ew[2]));
-            bad |= !(cfinite(xv) && cfinite(xe));
-            xw[0] = xv; ew[0] = xe;
-            d.v[o] = xv; d.eta[o] = xe;
-            if (partner >= 0) {
-                d.v[(size_t)i * P + partner] = cconj(xv);
-                d.eta[(size_t)i * P + partner] = cconj(xe);
+            if constexpr (DV) {
+                const double2 yv = d.v[o];
+                const double2 xv = cscale(TAB(d.tab_luv, k, i, 2),
+                                          caxpy(caxpy(yv, -TAB(d.tab_luv, k, i, 3), xw[1]), -TAB(d.tab_luv, k, i, 4), xw[2]));
+                bad |= !cfinite(xv);
+                xw[0] = xv;
+                d.v[o] = xv;
+                if (partner >= 0) d.v[(size_t)i * P + partner] = cconj(xv);
+            }
+            if constexpr (DE) {
+                const double2 ye = d.eta[o];
+                const double2 xe = cscale(TAB(d.tab_lue, k, i, 2),
+                                          caxpy(caxpy(ye, -TAB(d.tab_lue, k, i, 3), ew[1]), -TAB(d.tab_lue, k, i, 4), ew[2]));
+                bad |= !cfinite(xe);
+                ew[0] = xe;
+                d.eta[o] = xe;
+                if (partner >= 0) d.eta[(size_t)i * P + partner] = cconj(xe);
             }
         } else {
             xw[0] = cz(); ew[0] = cz();
-            d.v[pair] = cz(); d.eta[pair] = cz();
+            if constexpr (DV) d.v[pair] = cz();
+            if constexpr (DE) d.eta[pair] = cz();
         }
         if (i == N - 5) h_update(N - 2, false, true);          // one-sided eta row N-2
         const int jr = i + 2;
@@ -630,10 +660,18 @@ __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw,
     }
     if (bad) atomicOr(d.flag, 1);
     if (partner >= 0) {
-        d.v[(size_t)(N - 1) * P + partner] = cz(); d.eta[(size_t)(N - 1) * P + partner] = cz();
-        d.v[partner] = cz(); d.eta[partner] = cz();
+        if constexpr (DV) { d.v[(size_t)(N - 1) * P + partner] = cz(); d.v[partner] = cz(); }
+        if constexpr (DE) { d.eta[(size_t)(N - 1) * P + partner] = cz(); d.eta[partner] = cz(); }
     }
-    reconstruct_pair(d, pair, m, al, partner);
+    return true;
+}
+
+template <int MODE>
+__device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw, const int idx) {
+    int pair;
+    double m, al;
+    long long partner;
+    if (line_sweeps<MODE, 0>(d, k, ja, jw, idx, pair, m, al, partner)) reconstruct_pair(d, pair, m, al, partner);
 }
 
 // Kernel variants: a register budget from launch bounds (threads per block,
@@ -646,6 +684,26 @@ template <int MODE, int NREG>
 __global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k, int ja, int jw) {
     line_body<MODE>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
 }
+// Split variant for few pairs (a short line phase is bound by the latency
+// of one thread's radial recurrences): blocks of 64 threads, the first warp
+// advances v and the second eta of the same 32 pairs, then, after the block
+// barrier, the first warp rebuilds u and w.  The same arithmetic per field
+// as k_line.
+template <int MODE>
+__global__ void __launch_bounds__(64) k_line_s(TcDev d, int k, int ja, int jw) {
+    const int lane = threadIdx.x & 31;
+    const bool vrole = threadIdx.x < 32;
+    const int idx = blockIdx.x * 32 + lane;
+    int pair = 0;
+    double m = 0.0, al = 0.0;
+    long long partner = -1;
+    bool act;
+    if (vrole) act = line_sweeps<MODE, 1>(d, k, ja, jw, idx, pair, m, al, partner);
+    else act = line_sweeps<MODE, 2>(d, k, ja, jw, idx, pair, m, al, partner);
+    __syncthreads();
+    if (vrole && act) reconstruct_pair(d, pair, m, al, partner);
+}
+
 // Many cases in one launch: blocks of 128 threads, bmap[block] = (case,
 // block within the case), the case's descriptor from ds.
 template <int MODE>
@@ -1016,6 +1074,13 @@ void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int ja, int jw)
     // registers (2007: 7 resident blocks, 448 threads per SM, which splits
     // 131 k pairs into 1.9 waves instead of 1.7)
     const int v = d.line_block > 0 ? d.line_block : 128;
+    if (v == 3001) {                    // split: 32 pairs per 64-thread block
+        const int g = (d.Nz * jw + 31) / 32;
+        if (d.prec == 1) k_line_s<1><<<g, 64, 0, s>>>(d, k, ja, jw);
+        else if (d.prec == 2) k_line_s<2><<<g, 64, 0, s>>>(d, k, ja, jw);
+        else k_line_s<0><<<g, 64, 0, s>>>(d, k, ja, jw);
+        return;
+    }
     const int bs = v == 2007 ? 64 : (v > 1000 ? 128 : v);
     const int grid = (d.Nz * jw + bs - 1) / bs;
     switch (d.prec * 10 + (v == 1003 ? 1 : v == 1004 ? 2 : v == 2007 ? 3 : 0)) {
