@@ -59,6 +59,10 @@ def parse():
                         "kernels at the full pair count with a smaller device footprint)")
     p.add_argument("--column-groups", type=int, default=0,
                    help="pin the column groups of the step graph (0: chosen by timing)")
+    p.add_argument("--line-variant", type=int, default=0,
+                   help="pin the line-kernel variant (0: chosen by timing; the launch shape changes no bits)")
+    p.add_argument("--ztile", type=int, default=0,
+                   help="pin the z tile of the z kernels (0: chosen by timing)")
     return p.parse_args()
 
 
@@ -337,8 +341,8 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False,
     tc.tc_set_field(h, tc.TC_FIELD_V, v)
     tc.tc_set_field(h, tc.TC_FIELD_ETA, e)
     W0 = tc.tc_get_field(h, tc.TC_FIELD_MEAN_W)
-    if args.column_groups:
-        tc.tc_set_tiles(h, 0, 0, args.column_groups)
+    if args.column_groups or args.line_variant or args.ztile:
+        tc.tc_set_tiles(h, args.ztile, args.line_variant, args.column_groups)
     tc.tc_step(h, max(args.warmup, 3))
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if measure_clocks else None
