@@ -32,6 +32,11 @@
 #include "tc_dfloat.h"
 #include <type_traits>
 
+// threads per block of the paired theta rows (k_rows2)
+#ifndef TC_ROWS2_THREADS
+#define TC_ROWS2_THREADS 256
+#endif
+
 // float64 state -> arithmetic type of the transform; float and double-float
 // through integer bit operations (the float64 pipe also does conversions)
 template <typename T> __device__ __forceinline__ T from_f64(double x);
@@ -770,6 +775,112 @@ __device__ __forceinline__ void rows_body(const TcDev& d, const int q, const int
         for (int j = valid ? tg.tid : Nh; j < Nh; j += tg.nth) unpack_full(s2, j, 2);   // uw, vw
     }
 }
+// ---- k_rows2: two theta rows at once, every transform of full length -------
+// The rows q0 = 2 qp and q1 = q0 + 1 of plane r (a row past Mz computes on
+// zeros and stores nothing).  Each real signal pairs with another of the same
+// two rows in one complex transform of length Mt:
+//   inverse: u + i v of q0, u + i v of q1, w(q0) + i w(q1)   (3 columns)
+//   forward: (uu - vv) + i uv and uw + i vw of q0, the same of q1, and
+//            (ww - vv)(q0) + i (ww - vv)(q1)                   (5 columns)
+// A real signal's spectrum is Hermitian, so the input of column a + i b is
+// A_p + i B_p for p < Nh and conj(A_(Mt-p)) + i conj(B_(Mt-p)) for
+// p > Mt - Nh; the outputs split as A_j = (Z_j + conj Z_(Mt-j))/2 and
+// B_j = (Z_j - conj Z_(Mt-j))/(2i).  With all columns of one length, every
+// stage is one loop over the butterflies of all columns (no half-length
+// transform with its pre- and post-twiddles, and no second butterfly shape
+// in the stage loop).  Shared memory: two sides of 5 columns of Mt.  Used for
+// the float32 rows of the mixed form.
+template <typename T>
+__device__ __forceinline__ void rows2_body(const TcDev& d, const int qp, const int r, const TG tg, const int sub) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Mt = d.Mt, Nh = d.Nh, Mz = d.Mz, Nr = d.Nr;
+    C* A = reinterpret_cast<C*>(smem_raw) + (size_t)sub * 10 * Mt;
+    C* B = A + 5 * Mt;
+    const int q0 = 2 * qp;
+    const bool v0 = q0 < Mz, v1 = q0 + 1 < Mz;
+    const C* zb = reinterpret_cast<const C*>(d.zbuf);
+    const size_t fs = (size_t)Nr * Mz * Nh;                        // field stride of zbuf
+    const C* row0 = zb + ((size_t)r * Mz + (v0 ? q0 : 0)) * Nh;     // u of row q0
+    const C* row1 = zb + ((size_t)r * Mz + (v1 ? q0 + 1 : 0)) * Nh; // u of row q1
+    // column input from the spectra a, b of two real signals
+    auto herm = [&](const C* a, const C* b, bool va, bool vb, int p) -> C {
+        C z;
+        z.x = 0; z.y = 0;
+        if (p == 0) {
+            if (va) z.x = a[0].x;
+            if (vb) z.y = b[0].x;
+        } else if (p < Nh) {
+            C U, V;
+            U.x = 0; U.y = 0; V.x = 0; V.y = 0;
+            if (va) U = a[p];
+            if (vb) V = b[p];
+            z.x = U.x - V.y; z.y = U.y + V.x;
+        } else if (p > Mt - Nh) {
+            const int j = Mt - p;
+            C U, V;
+            U.x = 0; U.y = 0; V.x = 0; V.y = 0;
+            if (va) U = a[j];
+            if (vb) V = b[j];
+            z.x = U.x + V.y; z.y = V.x - U.y;
+        }
+        return z;
+    };
+    for (int p = tg.tid; p < Mt; p += tg.nth) {
+        A[p] = herm(row0, row0 + fs, v0, v0, p);                    // u + i v of q0
+        A[Mt + p] = herm(row1, row1 + fs, v1, v1, p);               // u + i v of q1
+        A[2 * Mt + p] = herm(row0 + 2 * fs, row1 + 2 * fs, v0, v1, p);   // w(q0) + i w(q1)
+    }
+    __syncthreads();
+    C* R = fft<T, +1, 0, true>(tg, A, B, 3, d.pt, twt<T>(d), d.twt_tan);
+    C* O = (R == A) ? B : A;
+    for (int p = tg.tid; p < Mt; p += tg.nth) {
+        const C a0 = R[p], a1 = R[Mt + p], ww = R[2 * Mt + p];
+        T bb[2];
+        #pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const C uv = e ? a1 : a0;
+            const T u = uv.x, v = uv.y, w = e ? ww.y : ww.x;
+            const T vv = v * v;
+            C b0, b1;
+            b0.x = u * u - vv; b0.y = u * v;         // uu - vv, uv
+            b1.x = u * w; b1.y = v * w;              // uw, vw
+            bb[e] = w * w - vv;                      // ww - vv
+            O[(2 * e) * Mt + p] = b0;
+            O[(2 * e + 1) * Mt + p] = b1;
+        }
+        C z; z.x = bb[0]; z.y = bb[1];
+        O[4 * Mt + p] = z;
+    }
+    __syncthreads();
+    const C* S = fft<T, -1, 0>(tg, O, R, 5, d.pt, twt<T>(d), d.twt_tan);
+    C* pb = reinterpret_cast<C*>(d.pbuf);
+    const size_t ps = (size_t)Nr * Mz * Nh;                        // product stride of pbuf
+    C* out0 = pb + ((size_t)r * Mz + q0) * Nh;
+    const T h = (T)0.5;
+    for (int j = tg.tid; j < Nh; j += tg.nth) {
+        const int jm = j == 0 ? 0 : Mt - j;
+        #pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const C cj = S[c * Mt + j], cm = S[c * Mt + jm];
+            C x1, x2;
+            x1.x = h * (cj.x + cm.x); x1.y = h * (cj.y - cm.y);
+            x2.x = h * (cj.y + cm.y); x2.y = -h * (cj.x - cm.x);
+            if (c < 4) {                             // two products of one row
+                const int e = c >> 1, slot = 2 * (c & 1);
+                if (e ? v1 : v0) {
+                    C* o = out0 + (size_t)e * Nh + j;
+                    o[slot * ps] = x1;
+                    o[(slot + 1) * ps] = x2;
+                }
+            } else {                                 // ww - vv of both rows
+                if (v0) out0[4 * ps + j] = x1;
+                if (v1) out0[4 * ps + Nh + j] = x2;
+            }
+        }
+    }
+}
+
 // rpb rows per block (short rows: more rows per block keep the threads of a
 // block busy), blockDim.x / rpb threads per row.
 __device__ __forceinline__ TG row_group(int rpb, int& sub) {
@@ -789,6 +900,21 @@ __global__ void __launch_bounds__(256) k_rows_b(const TcDev* __restrict__ ds, co
     int sub;
     const TG tg = row_group(rpb, sub);
     rows_body<T, LAYOUT, FUSE>(ds[m.x], blockIdx.x * rpb + sub, m.y, tg, sub);
+}
+// gpb row pairs per block, blockDim.x / gpb threads per pair
+template <typename T>
+__global__ void __launch_bounds__(TC_ROWS2_THREADS) k_rows2(TcDev d, int gpb) {
+    int sub;
+    const TG tg = row_group(gpb, sub);
+    rows2_body<T>(d, blockIdx.x * gpb + sub, blockIdx.y, tg, sub);
+}
+template <typename T>
+__global__ void __launch_bounds__(TC_ROWS2_THREADS) k_rows2_b(const TcDev* __restrict__ ds, const int2* __restrict__ ymap,
+                                                              int gpb) {
+    const int2 m = ymap[blockIdx.y];
+    int sub;
+    const TG tg = row_group(gpb, sub);
+    rows2_body<T>(ds[m.x], blockIdx.x * gpb + sub, m.y, tg, sub);
 }
 
 // ---- k_zfwd: pbuf -> spectral products, scaled by 1/(Mt Mz) (float64: already in pbuf) ----
@@ -866,6 +992,18 @@ static int rows_per_block(const TcDev& d) {
     while (rpb < 8 && (rpb * 2) * d.Mt <= 384) rpb *= 2;
     return rpb;
 }
+// Float32 theta rows in pairs (k_rows2) where two sides of 5 columns fit the
+// 200 KB of one block; row pairs per block: about 768 points per block, up
+// to 8 pairs.
+template <typename T>
+static bool rows_paired(const TcDev& d) {
+    return std::is_same<T, float>::value && 10 * (size_t)d.Mt * sizeof(typename V2<T>::t) <= 200 * 1024;
+}
+static int row_pairs_per_block(const TcDev& d) {
+    int gpb = 1;
+    while (gpb < 8 && (gpb * 2) * 2 * d.Mt <= 768) gpb *= 2;
+    return gpb;
+}
 
 template <typename T>
 static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0, int ntiles) {
@@ -885,6 +1023,12 @@ static void plane_kernel_t(const TcDev& d, int which, cudaStream_t s, int tile0,
         else k_zinv<T, 1><<<g, 256, smz, s>>>(d, d.u, d.v, d.w, tile0);
     } else if (which == 1) {
         constexpr bool fuse = !std::is_same<T, dfloat>::value;
+        if (rows_paired<T>(d)) {
+            const int gpb = row_pairs_per_block(d);
+            const dim3 g(((d.Mz + 1) / 2 + gpb - 1) / gpb, d.Nr);
+            k_rows2<T><<<g, TC_ROWS2_THREADS, gpb * 10 * (size_t)d.Mt * sizeof(C), s>>>(d, gpb);
+            return;
+        }
         const int rpb = rows_per_block(d);
         const dim3 g((d.Mz + rpb - 1) / rpb, d.Nr);
         if (layout == 5) k_rows<T, 5, fuse><<<g, 256, rpb * smr, s>>>(d, rpb);
@@ -922,6 +1066,12 @@ static void plane_kernel_batch_t(const TcDev& d0, const TcDev* ds, const int2* y
         else k_zinv_b<T, 1><<<g, 256, smz, s>>>(ds, ymap);
     } else if (which == 1) {
         constexpr bool fuse = !std::is_same<T, dfloat>::value;
+        if (rows_paired<T>(d0)) {
+            const int gpb = row_pairs_per_block(d0);
+            const dim3 g(((d0.Mz + 1) / 2 + gpb - 1) / gpb, nplanes);
+            k_rows2_b<T><<<g, TC_ROWS2_THREADS, gpb * 10 * (size_t)d0.Mt * sizeof(C), s>>>(ds, ymap, gpb);
+            return;
+        }
         const int rpb = rows_per_block(d0);
         const dim3 g((d0.Mz + rpb - 1) / rpb, nplanes);
         if (layout == 5) k_rows_b<T, 5, fuse><<<g, 256, rpb * smr, s>>>(ds, ymap, rpb);
@@ -954,5 +1104,6 @@ static cudaError_t plane_attributes_t() {
     set((const void*)k_zfwd_b<T, 0>); set((const void*)k_zfwd_b<T, 1>); set((const void*)k_zfwd_b<T, 2>);
     if constexpr (std::is_same<T, double>::value) set((const void*)k_zfwd_b<T, 3>);
     set((const void*)k_rows_b<T, 5, fuse>); set((const void*)k_rows_b<T, 4, fuse>);
+    if constexpr (std::is_same<T, float>::value) { set((const void*)k_rows2<T>); set((const void*)k_rows2_b<T>); }
     return e;
 }
