@@ -215,8 +215,24 @@ int tc_set_tiles(tc_handle* h, int ztile, int line_variant, int chunks);
 /* The launch shapes in use (after the autotuner): z tile, line-kernel
  * variant and column groups of the step graph (1: no overlap).  Any pointer
  * may be NULL.  A step graph launches 15 kernels without groups and
- * 7 + 8 * chunks with them. */
+ * 7 + 8 * chunks with them, 3 more with the deferred RK memory below. */
 int tc_get_tiles(const tc_handle* h, int* ztile, int* line_variant, int* chunks);
+
+/* Deferred RK memory (double-float and mixed forms; no counterpart in the
+ * paper, same bits either way).  The implicit part of the next substep's
+ * low-storage RK memory, H += (beta_k + alpha_k+1) dt L x^(k+1) (Sec. 2.3;
+ * L the implicit band of Eq. 6 or 7), needs only the new v and eta.  With
+ * the deferral on, the line kernel leaves it out and a kernel of its own
+ * adds it beside the next substep's theta rows, whose float32 or
+ * double-float work leaves the float64 pipe idle; within one tc_step call
+ * the last substep's term of a step runs beside the next step's first
+ * theta rows, and the last one is completed before tc_step returns.
+ *   mode: -1 chosen by timing with the autotuner (the default; off without
+ *         it), 0 off, 1 on.  No effect in the float64 form.
+ * tc_get_rk_deferral reports whether it is on (1) or off (0).  TC_ERR_ARG
+ * for a null handle or another mode; a captured step graph is rebuilt. */
+int tc_set_rk_deferral(tc_handle* h, int mode);
+int tc_get_rk_deferral(const tc_handle* h, int* on);
 
 /* Device bytes held by the handle. */
 size_t tc_device_bytes(const tc_handle* h);

@@ -101,6 +101,10 @@ def lib():
     L.tc_load_state.argtypes = [vp, vp, sz]
     L.tc_set_tiles.restype = i
     L.tc_set_tiles.argtypes = [vp, i, i, i]
+    L.tc_set_rk_deferral.restype = i
+    L.tc_set_rk_deferral.argtypes = [vp, i]
+    L.tc_get_rk_deferral.restype = i
+    L.tc_get_rk_deferral.argtypes = [vp, ctypes.POINTER(i)]
     L.tc_get_tiles.restype = i
     L.tc_get_tiles.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.tc_device_bytes.restype = sz
@@ -306,9 +310,24 @@ def tc_get_tiles(h):
     return z.value, l.value, c.value
 
 
-def step_kernels(chunks):
-    """Kernels one step graph launches."""
-    return 15 if chunks <= 1 else 7 + 8 * chunks
+def step_kernels(chunks, rk_deferred=False):
+    """Kernels one step launches: the step graph, plus the three RK-memory
+    kernels with the deferred RK memory."""
+    return (15 if chunks <= 1 else 7 + 8 * chunks) + (3 if rk_deferred else 0)
+
+
+def tc_set_rk_deferral(h, mode):
+    """Deferred RK memory of the double-float and mixed forms: -1 chosen by
+    timing (the default), 0 off, 1 on (no effect in the float64 form; same
+    bits either way)."""
+    return _check(lib().tc_set_rk_deferral(h, int(mode)))
+
+
+def tc_get_rk_deferral(h):
+    """Whether the deferred RK memory is on (True) for the captured steps."""
+    on = ctypes.c_int()
+    _check(lib().tc_get_rk_deferral(h, ctypes.byref(on)))
+    return bool(on.value)
 
 
 def tc_device_bytes(h):

@@ -321,8 +321,7 @@ int upload(tc_handle* h, const T*& dst, const std::vector<T>& src) {
 }
 
 void free_all(tc_handle* h) {
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
+    tcx::drop_graphs(h);
     tcx::release_pipeline(h);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
@@ -334,7 +333,6 @@ void free_all(tc_handle* h) {
 // Nz, precision).  The choice changes no arithmetic.
 std::mutex g_tune_mu;
 std::map<std::array<int, 4>, std::pair<int, int>> g_tune;
-std::map<std::array<int, 4>, int> g_tune_chunks;   // column groups chosen by tc_step
 
 int autotune(tc_handle* h) {
     TcDev& d = h->d;
@@ -649,6 +647,9 @@ int prepare_pipeline(tc_handle* h) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evm, cudaEventDisableTiming);
     for (auto& ev : h->evj)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->srk, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evrk0, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->evrk1, cudaEventDisableTiming);
     h->pipe_ready = true;                // lets release_pipeline free what exists
     if (e != cudaSuccess) {
         release_pipeline(h);
@@ -669,6 +670,11 @@ void release_pipeline(tc_handle* h) {
     if (h->evm) cudaEventDestroy(h->evm);
     h->evm = nullptr;
     for (auto& ev : h->evj) { if (ev) cudaEventDestroy(ev); ev = nullptr; }
+    if (h->srk) cudaStreamDestroy(h->srk);
+    if (h->evrk0) cudaEventDestroy(h->evrk0);
+    if (h->evrk1) cudaEventDestroy(h->evrk1);
+    h->srk = nullptr;
+    h->evrk0 = h->evrk1 = nullptr;
     h->pipe_ready = false;
 }
 
@@ -692,15 +698,52 @@ int pipeline_chunks(const tc_handle* h) {
 // must precede the z inverse of group 0 (its (0,0) slot holds U, W).  The
 // theta rows of each substep wait for every group.  The line kernels of
 // alternate groups use two streams so that they overlap too.
-void launch_step(tc_handle* h, cudaStream_t s) {
+// Deferred RK memory (double-float and mixed forms, inside a captured step):
+// the line kernels leave out the implicit part of the next RK memory, and
+// k_rk_memory adds it for substep k - 1 on its own stream beside the theta
+// rows of substep k, whose float32 work leaves the float64 pipe idle; the
+// line kernel of substep k waits for it.  The last substep's memory is
+// completed at the end of the step.  Same bits as the full line kernel.
+bool defer_rk(const tc_handle* h) {
+    const int m = h->rk_defer >= 0 ? h->rk_defer : h->rk_defer_auto;
+    return h->pipe_ready && h->d.prec != TC_PREC_FP64 && m == 1;
+}
+void drop_graphs(tc_handle* h) {
+    for (cudaGraphExec_t* g : {&h->graph, &h->graph_first, &h->graph_next}) {
+        if (*g) cudaGraphExecDestroy(*g);
+        *g = nullptr;
+    }
+}
+static void rk_fork(tc_handle* h, int kprev, cudaStream_t s) {
+    cudaEventRecord(h->evrk0, s);
+    cudaStreamWaitEvent(h->srk, h->evrk0, 0);
+    tc_launch_rk_memory(h->d, kprev, h->srk, 0, h->d.Nh, true);
+    cudaEventRecord(h->evrk1, h->srk);
+}
+static void line_chunk(const tc_handle* h, int k, cudaStream_t s, int ja, int jw) {
+    if (defer_rk(h)) tc_launch_line_chunk_deferred(h->d, k, s, ja, jw);
+    else tc_launch_line_chunk(h->d, k, s, ja, jw);
+}
+
+// With the deferred RK memory, `lead` starts the step with the previous
+// step's last RK memory (beside the first theta rows) and `trail` ends it with
+// this step's own; the self-contained step has trail only.
+void launch_step(tc_handle* h, cudaStream_t s, bool lead, bool trail) {
     TcDev& d = h->d;
     const int C = h->pipe_ready ? pipeline_chunks(h) : 1;
+    const bool defer = defer_rk(h);
+    auto pending = [&](int k) { return defer && (k > 0 || lead); };   // an RK memory to add before line k
     if (C <= 1) {
         for (int k = 0; k < 3; ++k) {
-            tc_launch_plane_phase(d, s);
-            tc_launch_line_phase(d, k, s);
+            tc_launch_plane_kernel(d, 0, s);
+            if (pending(k)) rk_fork(h, k > 0 ? k - 1 : 2, s);
+            tc_launch_plane_kernel(d, 1, s);
+            tc_launch_plane_kernel(d, 2, s);
+            if (pending(k)) cudaStreamWaitEvent(s, h->evrk1, 0);
+            line_chunk(h, k, s, 0, d.Nh);
             tc_launch_mean_phase(d, k, s);
         }
+        if (defer && trail) tc_launch_rk_memory(d, 2, s, 0, d.Nh, false);
         return;
     }
     const int tpc = (d.Nh / d.ztile) / C;      // z tiles per group
@@ -708,6 +751,7 @@ void launch_step(tc_handle* h, cudaStream_t s) {
     cudaStream_t sM = h->aux[2], sZ = h->aux[3];
     tc_launch_plane_kernel(d, 0, s);           // z inverse of the first substep
     for (int k = 0; k < 3; ++k) {
+        if (pending(k)) rk_fork(h, k > 0 ? k - 1 : 2, s);
         tc_launch_plane_kernel(d, 1, s);       // theta rows and products
         for (int c = 0; c < C; ++c) {
             tc_launch_plane_kernel_tiles(d, 2, s, c * tpc, tpc);
@@ -719,7 +763,8 @@ void launch_step(tc_handle* h, cudaStream_t s) {
         for (int c = 0; c < C; ++c) {
             cudaStream_t sL = h->aux[c & 1];
             cudaStreamWaitEvent(sL, h->evz[c], 0);
-            tc_launch_line_chunk(d, k, sL, c * cw, cw);
+            if (pending(k)) cudaStreamWaitEvent(sL, h->evrk1, 0);
+            line_chunk(h, k, sL, c * cw, cw);
             cudaEventRecord(h->evl[c], sL);
             if (k < 2) {
                 cudaStreamWaitEvent(sZ, h->evl[c], 0);
@@ -732,23 +777,60 @@ void launch_step(tc_handle* h, cudaStream_t s) {
             cudaStreamWaitEvent(s, h->evj[a], 0);
         }
     }
+    if (defer && trail) tc_launch_rk_memory(d, 2, s, 0, d.Nh, false);
 }
 
-int ensure_graph(tc_handle* h) {
-    if (h->graph) return TC_OK;
-    int rc_;
-    if ((rc_ = prepare_pipeline(h))) return rc_;
+static int capture_step(tc_handle* h, bool lead, bool trail, cudaGraphExec_t* out) {
     cudaStream_t cs;
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    launch_step(h, cs);
+    launch_step(h, cs, lead, trail);
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (e != cudaSuccess) { cudaStreamDestroy(cs); set_err(std::string("graph capture: ") + cudaGetErrorString(e)); return TC_ERR_CUDA; }
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    unsigned long long flags = 0;
+    if (defer_rk(h)) {
+        // the deferred RK memory fills what the theta rows leave free: every
+        // other kernel node gets the highest priority, so that its blocks are
+        // dispatched first
+        int least = 0, greatest = 0;
+        size_t n = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+            cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess) {
+            std::vector<cudaGraphNode_t> nodes(n);
+            if (cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess) {
+                const void* rk = tc_rk_memory_kernel();
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType t;
+                    cudaKernelNodeParams kp;
+                    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+                    if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+                    cudaLaunchAttributeValue v{};
+                    v.priority = kp.func == rk ? least : greatest;
+                    cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v);
+                }
+                flags = cudaGraphInstantiateFlagUseNodePriority;
+            }
+        }
+        cudaGetLastError();
+    }
+    e = cudaGraphInstantiateWithFlags(out, g, flags);
     cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
-    if (e != cudaSuccess) { set_err(std::string("graph instantiate: ") + cudaGetErrorString(e)); return TC_ERR_CUDA; }
+    if (e != cudaSuccess) { *out = nullptr; set_err(std::string("graph instantiate: ") + cudaGetErrorString(e)); return TC_ERR_CUDA; }
+    return TC_OK;
+}
+
+// The self-contained step graph, and with the deferred RK memory the first
+// and following steps of a tc_step call.
+int ensure_graph(tc_handle* h) {
+    int rc_;
+    if ((rc_ = prepare_pipeline(h))) return rc_;
+    if (!h->graph && (rc_ = capture_step(h, false, true, &h->graph))) return rc_;
+    if (defer_rk(h)) {
+        if (!h->graph_first && (rc_ = capture_step(h, false, false, &h->graph_first))) return rc_;
+        if (!h->graph_next && (rc_ = capture_step(h, true, false, &h->graph_next))) return rc_;
+    }
     return TC_OK;
 }
 
@@ -852,6 +934,22 @@ int tc_get_tiles(const tc_handle* h, int* ztile, int* line_variant, int* chunks)
     return TC_OK;
 }
 
+int tc_set_rk_deferral(tc_handle* h, int mode) {
+    if (!h) { set_err("null handle"); return TC_ERR_ARG; }
+    if (mode < -1 || mode > 1) { set_err("mode must be -1 (chosen by timing), 0 or 1"); return TC_ERR_ARG; }
+    h->rk_defer = mode;
+    if (mode < 0) h->rk_defer_auto = -1;
+    tcx::drop_graphs(h);
+    return TC_OK;
+}
+
+int tc_get_rk_deferral(const tc_handle* h, int* on) {
+    if (!h || !on) { set_err("null handle or output"); return TC_ERR_ARG; }
+    const int m = h->rk_defer >= 0 ? h->rk_defer : h->rk_defer_auto;
+    *on = (h->d.prec != TC_PREC_FP64 && m == 1) ? 1 : 0;
+    return TC_OK;
+}
+
 int tc_set_tiles(tc_handle* h, int ztile, int line_variant, int chunks) {
     if (!h) { set_err("null handle"); return TC_ERR_ARG; }
     TcDev& d = h->d;
@@ -874,7 +972,7 @@ int tc_set_tiles(tc_handle* h, int ztile, int line_variant, int chunks) {
     if (ztile) d.ztile = ztile;
     if (line_variant) d.line_block = line_variant;
     if (chunks) h->chunks = chunks;
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    tcx::drop_graphs(h);
     return TC_OK;
 }
 
@@ -889,27 +987,48 @@ int tcx::check_flags(tc_handle* h) {
 using tcx::check_flags;
 
 namespace {
-// With the autotuner on and no grouping set, the first tc_step of three or
-// more steps runs one step with each candidate grouping (1 and 2 column
-// groups), timed with events, and keeps the faster for this handle and the
-// shape class.  Every grouping gives the same bits, so the tuning steps are
-// ordinary steps.
+// With the autotuner on, the first tc_step of three or more steps runs one
+// self-contained step with each candidate launch plan not pinned by the
+// caller: 1 and 2 column groups and, in the double-float and mixed forms,
+// the RK memory's implicit part in the line kernel or deferred beside the
+// theta rows.  Each is timed with events; the fastest is kept for this
+// handle and the shape class.  Every plan gives the same bits, so the tuning
+// steps are ordinary steps.
+std::map<std::array<int, 4>, std::pair<int, int>> g_tune_plan;   // (column groups, deferral)
+
 int tune_chunks(tc_handle* h, int nsteps, int* done) {
     *done = 0;
-    if (!h->prm.autotune || h->chunks > 0 || h->chunks_auto > 0) return TC_OK;
     TcDev& d = h->d;
+    const bool tune_c = h->chunks <= 0 && h->chunks_auto <= 0;
+    const bool tune_d = d.prec != TC_PREC_FP64 && h->rk_defer < 0 && h->rk_defer_auto < 0;
+    if (!h->prm.autotune) {
+        if (h->rk_defer_auto < 0) h->rk_defer_auto = 0;
+        return TC_OK;
+    }
+    if (!tune_c && !tune_d) return TC_OK;
     const std::array<int, 4> key = {d.Nr, 2 * d.Nh, d.Nz, d.prec};
-    {
+    if (h->chunks <= 0 && h->rk_defer < 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_chunks.find(key);
-        if (it != g_tune_chunks.end()) {
-            h->chunks_auto = it->second;
-            if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+        auto it = g_tune_plan.find(key);
+        if (it != g_tune_plan.end()) {
+            h->chunks_auto = it->second.first;
+            h->rk_defer_auto = it->second.second;
+            tcx::drop_graphs(h);
             return TC_OK;
         }
     }
-    if (!tcx::chunks_valid(h, 2)) { h->chunks_auto = 1; return TC_OK; }
-    if (nsteps < 3) return TC_OK;              // decide on a later, longer call
+    std::vector<int> cs, ds;
+    if (tune_c) { cs.push_back(1); if (tcx::chunks_valid(h, 2)) cs.push_back(2); }
+    else cs.push_back(h->chunks > 0 ? h->chunks : h->chunks_auto);
+    if (tune_d) { ds.push_back(0); ds.push_back(1); }
+    else ds.push_back(d.prec == TC_PREC_FP64 ? 0 : (h->rk_defer >= 0 ? h->rk_defer : h->rk_defer_auto));
+    if (cs.size() * ds.size() == 1) {
+        h->chunks_auto = cs[0];
+        h->rk_defer_auto = ds[0];
+        tcx::drop_graphs(h);
+        return TC_OK;
+    }
+    if (nsteps < (int)(cs.size() * ds.size()) + 1) return TC_OK;   // decide on a later, longer call
     cudaEvent_t a = nullptr, b = nullptr;
     struct Events {                      // destroyed on every exit
         cudaEvent_t *a, *b;
@@ -918,26 +1037,32 @@ int tune_chunks(tc_handle* h, int nsteps, int* done) {
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
     float best = 1e30f;
-    int bestc = 1;
-    for (int c : {1, 2}) {
-        h->chunks_auto = c;
-        if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
-        int rc = ensure_graph(h);
-        if (rc) return rc;
-        CK(cudaGraphUpload(h->graph, h->stream));
-        CK(cudaEventRecord(a, h->stream));
-        CK(cudaGraphLaunch(h->graph, h->stream));
-        CK(cudaEventRecord(b, h->stream));
-        CK(cudaEventSynchronize(b));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, a, b));
-        if (ms < best) { best = ms; bestc = c; }
-        ++*done;
+    int bestc = cs[0], bestd = ds[0];
+    for (int c : cs) {
+        for (int df : ds) {
+            h->chunks_auto = c;
+            h->rk_defer_auto = df;
+            tcx::drop_graphs(h);
+            int rc = ensure_graph(h);
+            if (rc) return rc;
+            CK(cudaGraphUpload(h->graph, h->stream));
+            CK(cudaEventRecord(a, h->stream));
+            CK(cudaGraphLaunch(h->graph, h->stream));
+            CK(cudaEventRecord(b, h->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (ms < best) { best = ms; bestc = c; bestd = df; }
+            ++*done;
+        }
     }
     h->chunks_auto = bestc;
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_chunks[key] = bestc;
+    h->rk_defer_auto = bestd;
+    tcx::drop_graphs(h);
+    if (h->chunks <= 0 && h->rk_defer < 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_plan[key] = {bestc, bestd};
+    }
     return TC_OK;
 }
 }  // namespace
@@ -1042,7 +1167,16 @@ int tc_step(tc_handle* h, int nsteps) {
     int done = 0;
     if ((rc = tune_chunks(h, nsteps, &done))) return rc;
     if ((rc = ensure_graph(h))) return rc;
-    for (int n = done; n < nsteps; ++n) CK(cudaGraphLaunch(h->graph, h->stream));
+    if (tcx::defer_rk(h) && nsteps > done) {
+        // the previous step's last RK memory runs beside the next step's
+        // first theta rows; the last one is completed after the final step
+        CK(cudaGraphLaunch(h->graph_first, h->stream));
+        for (int n = done + 1; n < nsteps; ++n) CK(cudaGraphLaunch(h->graph_next, h->stream));
+        tc_launch_rk_memory(h->d, 2, h->stream, 0, h->d.Nh, false);
+        CK(cudaGetLastError());
+    } else {
+        for (int n = done; n < nsteps; ++n) CK(cudaGraphLaunch(h->graph, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
     h->t += nsteps * h->d.dt;
     h->step += nsteps;
@@ -1159,7 +1293,7 @@ int tc_get_field(tc_handle* h, int which, int space, void* buf, size_t bytes) {
             double* p;
             if ((rc = dalloc(h, p, (size_t)d.Nr * d.Mz * d.Mt))) return rc;
             d.phys = p;
-            if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+            tcx::drop_graphs(h);
         }
         tc_launch_to_physical(d, src, h->stream);
         CK(cudaGetLastError());

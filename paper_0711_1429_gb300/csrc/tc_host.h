@@ -40,6 +40,17 @@ struct tc_handle {
     bool pipe_ready = false;
     cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t evz[TC_MAX_CHUNKS] = {}, evl[TC_MAX_CHUNKS] = {}, evm = nullptr, evj[4] = {};
+    // deferred RK memory (double-float and mixed forms): the implicit part of
+    // substep k's RK memory runs on srk beside the theta rows of substep k+1
+    // (rk_defer: -1 chosen by timing, 0 off, 1 on; rk_defer_auto: the
+    // timed choice).  tc_step then runs graph_first, graph_next (which
+    // starts the previous step's last RK memory beside its own theta rows)
+    // and completes the last one after the final step; `graph` is the
+    // self-contained step (the server launches it one step at a time).
+    cudaStream_t srk = nullptr;
+    cudaEvent_t evrk0 = nullptr, evrk1 = nullptr;
+    int rk_defer = -1, rk_defer_auto = -1;
+    cudaGraphExec_t graph_first = nullptr, graph_next = nullptr;
     // this rank's share of a case split across ranks (tc_split_set): radial
     // planes [r0, r1) of the plane phase, azimuthal columns [j0, j1) of the
     // line phase, and the products of its planes [TC_NPROD][r1-r0][Nz][Nh]
@@ -57,8 +68,11 @@ struct Range {
 };
 void set_err(const std::string& s);
 int ensure_init(tc_handle* h);                 // H_1 and u, w of the current state
-void launch_step(tc_handle* h, cudaStream_t s);  // the 15 kernels of one step
+// the kernels of one step (lead / trail: see the deferred RK memory above)
+void launch_step(tc_handle* h, cudaStream_t s, bool lead, bool trail);
 int ensure_graph(tc_handle* h);
+void drop_graphs(tc_handle* h);                // the captured steps (after a change of launch shapes)
+bool defer_rk(const tc_handle* h);            // deferred RK memory in the captured steps
 int prepare_pipeline(tc_handle* h);           // aux streams and events (before any capture)
 int pipeline_chunks(const tc_handle* h);      // column groups of the overlapped step (1: none)
 bool chunks_valid(const tc_handle* h, int c);

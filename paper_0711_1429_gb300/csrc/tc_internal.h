@@ -152,6 +152,13 @@ cudaError_t tc_probe_fma(double* fp64_tflops, double* fp32_tflops);
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s);
 // line phase of the pairs with azimuthal index j0 <= j < j0 + nj (all axial slots)
 void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int j0, int nj);
+// the same without the implicit part of the next RK memory (double-float and
+// mixed forms; float64 launches the full kernel), which tc_launch_rk_memory
+// then adds for the same pairs before the next substep's line kernel
+void tc_launch_line_chunk_deferred(const TcDev& d, int k, cudaStream_t s, int j0, int nj);
+// (background: in four blocks per SM, for a launch beside other kernels)
+void tc_launch_rk_memory(const TcDev& d, int k, cudaStream_t s, int j0, int nj, bool background);
+const void* tc_rk_memory_kernel();   // its kernel, to find its nodes in a captured graph
 void tc_launch_mean_phase(const TcDev& d, int k, cudaStream_t s);
 // line phase and mean flow of substep k for many cases of one precision form
 // (descriptors ds on the device): the line kernel in nblocks blocks of

@@ -424,11 +424,42 @@ __device__ __forceinline__ void inner_terms(const CT& pa, const CT& uv, const CT
     be = tadd(be, timag((T)2 * nut * mt * ri2, U));
 }
 
+// k^2 = alpha^2 + m^2/r^2 of the implicit eta band, rounded the same way in
+// every kernel that forms it
+__device__ __forceinline__ double k2_at(double m, double al, double ri) {
+    return __fma_rn(__dmul_rn(m, m), __dmul_rn(ri, ri), __dmul_rn(al, al));
+}
+
+// Implicit part of the next RK memory on row jr (SMR91 low storage):
+// H_(k+1) += (beta_k + alpha_(k+1)) dt L x^(k+1), with L the v band of row jr
+// (the per-pair table) or nu (l2 - d0 k^2) of the eta row, applied to the
+// window xw / ew of x^(k+1) on the row's five stencil points (k2w: k^2 at
+// those points).  The line kernel calls it during its back substitution; the
+// deferred form (k_rk_memory) calls it after a line kernel that left it out,
+// with the same operands, so both give the same bits.
+__device__ __forceinline__ void rk_memory_row(const TcDev& d, int pair, int jr, const double2* xw, const double2* ew,
+                                              const double* k2w, double hdt, double hdtnu, bool do_v, bool do_e) {
+    const size_t o = (size_t)jr * d.npairs + pair;
+    if (do_v) {
+        double2 acc = cz();
+        for (int s = 0; s < 5; ++s) acc = caxpy(acc, TAB(d.tab_lv, 0, jr, s), xw[s]);
+        d.Hv[o] = caxpy(d.Hv[o], hdt, acc);
+    }
+    if (do_e) {
+        double2 acc = cz();
+        for (int s = 0; s < 5; ++s)
+            acc = caxpy(acc, fma(-d.d0[jr * 5 + s], k2w[s], d.l2[jr * 5 + s]), ew[s]);
+        d.He[o] = caxpy(d.He[o], hdtnu, acc);
+    }
+}
+
 // The sweeps of one pair (ROLE 0: v and eta; 1: v only; 2: eta only, for the
 // kernel in which one thread advances v and another eta of the same pair);
 // returns false for a thread without a pair to evolve.  The arithmetic of
-// each field is the same in every role.
-template <int MODE, int ROLE>
+// each field is the same in every role.  With NOH the implicit part of the
+// next RK memory is left to k_rk_memory (launched after this kernel, before
+// the next substep's line kernel).
+template <int MODE, int ROLE, bool NOH = false>
 __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int jw, const int idx, int& pair_out,
                                             double& m_out, double& al_out, long long& partner_out) {
     constexpr bool MIXED = (MODE == 1);
@@ -603,31 +634,16 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
     double k2w[5];
     for (int s = 0; s < 5; ++s) { xw[s] = cz(); ew[s] = cz(); k2w[s] = 0.0; }
     bool bad = false;
-    const double k2N = al * al + m * m * d.rinv[N - 1] * d.rinv[N - 1];
-    xw[0] = cz(); ew[0] = cz(); k2w[0] = k2N;
+    if constexpr (!NOH) k2w[0] = k2_at(m, al, d.rinv[N - 1]);
     if constexpr (DV) d.v[(size_t)(N - 1) * P + pair] = cz();
     if constexpr (DE) d.eta[(size_t)(N - 1) * P + pair] = cz();
     const double hdtnu = hdt * nu;
     auto h_update = [&](int jr, bool do_v, bool do_e) {
-        const size_t o = (size_t)jr * P + pair;
-        do_v = do_v && DV;
-        do_e = do_e && DE;
-        if (do_v) {
-            double2 acc = cz();
-            for (int s = 0; s < 5; ++s) acc = caxpy(acc, TAB(d.tab_lv, 0, jr, s), xw[s]);
-            d.Hv[o] = caxpy(d.Hv[o], hdt, acc);
-        }
-        if (do_e) {
-            double2 acc = cz();
-            for (int s = 0; s < 5; ++s)
-                acc = caxpy(acc, fma(-d.d0[jr * 5 + s], k2w[s], d.l2[jr * 5 + s]), ew[s]);
-            d.He[o] = caxpy(d.He[o], hdtnu, acc);
-        }
+        if constexpr (!NOH) rk_memory_row(d, pair, jr, xw, ew, k2w, hdt, hdtnu, do_v && DV, do_e && DE);
     };
     for (int i = N - 2; i >= 0; --i) {
         for (int s = 4; s > 0; --s) { xw[s] = xw[s - 1]; ew[s] = ew[s - 1]; k2w[s] = k2w[s - 1]; }
-        const double ri = d.rinv[i];
-        k2w[0] = al * al + m * m * ri * ri;
+        if constexpr (!NOH) k2w[0] = k2_at(m, al, d.rinv[i]);
         if (i >= 1) {
             const size_t o = (size_t)i * P + pair;
             if constexpr (DV) {
@@ -666,30 +682,30 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
     return true;
 }
 
-template <int MODE>
+template <int MODE, bool NOH = false>
 __device__ __forceinline__ void line_body(const TcDev& d, int k, int ja, int jw, const int idx) {
     int pair;
     double m, al;
     long long partner;
-    if (line_sweeps<MODE, 0>(d, k, ja, jw, idx, pair, m, al, partner)) reconstruct_pair(d, pair, m, al, partner);
+    if (line_sweeps<MODE, 0, NOH>(d, k, ja, jw, idx, pair, m, al, partner)) reconstruct_pair(d, pair, m, al, partner);
 }
 
 // Kernel variants: a register budget from launch bounds (threads per block,
 // resident blocks per SM), or an explicit register cap.
-template <int MODE, int MAXT, int MINB>
+template <int MODE, int MAXT, int MINB, bool NOH = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_line(TcDev d, int k, int ja, int jw) {
-    line_body<MODE>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
+    line_body<MODE, NOH>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
 }
-template <int MODE, int NREG>
+template <int MODE, int NREG, bool NOH = false>
 __global__ void __maxnreg__(NREG) k_line_r(TcDev d, int k, int ja, int jw) {
-    line_body<MODE>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
+    line_body<MODE, NOH>(d, k, ja, jw, blockIdx.x * blockDim.x + threadIdx.x);
 }
 // Split variant for few pairs (a short line phase is bound by the latency
 // of one thread's radial recurrences): blocks of 64 threads, the first warp
 // advances v and the second eta of the same 32 pairs, then, after the block
 // barrier, the first warp rebuilds u and w.  The same arithmetic per field
 // as k_line.
-template <int MODE>
+template <int MODE, bool NOH = false>
 __global__ void __launch_bounds__(64) k_line_s(TcDev d, int k, int ja, int jw) {
     const int lane = threadIdx.x & 31;
     const bool vrole = threadIdx.x < 32;
@@ -698,10 +714,51 @@ __global__ void __launch_bounds__(64) k_line_s(TcDev d, int k, int ja, int jw) {
     double m = 0.0, al = 0.0;
     long long partner = -1;
     bool act;
-    if (vrole) act = line_sweeps<MODE, 1>(d, k, ja, jw, idx, pair, m, al, partner);
-    else act = line_sweeps<MODE, 2>(d, k, ja, jw, idx, pair, m, al, partner);
+    if (vrole) act = line_sweeps<MODE, 1, NOH>(d, k, ja, jw, idx, pair, m, al, partner);
+    else act = line_sweeps<MODE, 2, NOH>(d, k, ja, jw, idx, pair, m, al, partner);
     __syncthreads();
     if (vrole && act) reconstruct_pair(d, pair, m, al, partner);
+}
+
+// The implicit part of the next RK memory (rk_memory_row) for the pairs of
+// the columns ja .. ja + jw - 1, after a line kernel of substep k launched
+// with NOH: one thread per pair walks its radial line downwards like the
+// back substitution, reading x^(k+1) (v, eta) instead of computing it.  It
+// needs only the results of that line kernel, so it can run beside the next
+// substep's plane phase.
+// Grid-stride over the pairs: launched beside the theta rows it runs in few
+// blocks (four per SM), so that it takes mostly what the rows leave free.
+__global__ void __launch_bounds__(128) k_rk_memory(TcDev d, int k, int ja, int jw) {
+    const int N = d.Nr;
+    const size_t P = d.npairs;
+    const int kn = (k + 1) % 3;
+    const double hdt = (d.rk_beta[k] + d.rk_alpha[kn]) * d.dt;
+    const double hdtnu = hdt * d.nu;
+    const int n = d.Nz * jw;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int pair = (idx / jw) * d.Nh + ja + idx % jw;
+        double m, al;
+        long long partner;
+        if (!pair_info(d, pair, m, al, partner)) continue;
+        double2 xw[5], ew[5];
+        double k2w[5];
+        for (int s = 0; s < 5; ++s) { xw[s] = cz(); ew[s] = cz(); k2w[s] = 0.0; }
+        k2w[0] = k2_at(m, al, d.rinv[N - 1]);
+        for (int i = N - 2; i >= 0; --i) {
+            for (int s = 4; s > 0; --s) { xw[s] = xw[s - 1]; ew[s] = ew[s - 1]; k2w[s] = k2w[s - 1]; }
+            k2w[0] = k2_at(m, al, d.rinv[i]);
+            if (i >= 1) {
+                xw[0] = d.v[(size_t)i * P + pair];
+                ew[0] = d.eta[(size_t)i * P + pair];
+            } else {
+                xw[0] = cz(); ew[0] = cz();
+            }
+            if (i == N - 5) rk_memory_row(d, pair, N - 2, xw, ew, k2w, hdt, hdtnu, false, true);
+            const int jr = i + 2;
+            if (i <= N - 5 && jr >= 2) rk_memory_row(d, pair, jr, xw, ew, k2w, hdt, hdtnu, true, true);
+            if (i == 0) rk_memory_row(d, pair, 1, xw, ew, k2w, hdt, hdtnu, false, true);
+        }
+    }
 }
 
 // Many cases in one launch: blocks of 128 threads, bmap[block] = (case,
@@ -1067,37 +1124,54 @@ void tc_launch_setup_tables(const TcDev& d, cudaStream_t s) {
 
 void tc_launch_line_phase(const TcDev& d, int k, cudaStream_t s) { tc_launch_line_chunk(d, k, s, 0, d.Nh); }
 
-void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int ja, int jw) {
-    // line_block encodes the variant: 64/128/256 threads with the register
-    // budget of one 256-thread block per SM; 128 threads with a budget for 3
-    // (1003) or 4 (1004) resident blocks per SM; 64 threads capped at 144
-    // registers (2007: 7 resident blocks, 448 threads per SM, which splits
-    // 131 k pairs into 1.9 waves instead of 1.7)
+// line_block encodes the variant: 64/128/256 threads with the register
+// budget of one 256-thread block per SM; 128 threads with a budget for 3
+// (1003) or 4 (1004) resident blocks per SM; 64 threads capped at 144
+// registers (2007: 7 resident blocks, 448 threads per SM, which splits 131 k
+// pairs into 1.9 waves instead of 1.7); 3001: the split variant.  NOH
+// (double-float and mixed forms only): without the implicit RK-memory term.
+template <int MODE, bool NOH>
+static void line_chunk_t(const TcDev& d, int k, cudaStream_t s, int ja, int jw) {
     const int v = d.line_block > 0 ? d.line_block : 128;
     if (v == 3001) {                    // split: 32 pairs per 64-thread block
-        const int g = (d.Nz * jw + 31) / 32;
-        if (d.prec == 1) k_line_s<1><<<g, 64, 0, s>>>(d, k, ja, jw);
-        else if (d.prec == 2) k_line_s<2><<<g, 64, 0, s>>>(d, k, ja, jw);
-        else k_line_s<0><<<g, 64, 0, s>>>(d, k, ja, jw);
+        k_line_s<MODE, NOH><<<(d.Nz * jw + 31) / 32, 64, 0, s>>>(d, k, ja, jw);
         return;
     }
     const int bs = v == 2007 ? 64 : (v > 1000 ? 128 : v);
     const int grid = (d.Nz * jw + bs - 1) / bs;
-    switch (d.prec * 10 + (v == 1003 ? 1 : v == 1004 ? 2 : v == 2007 ? 3 : 0)) {
-        case 0:  k_line<0, 256, 1><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 1:  k_line<0, 128, 3><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 2:  k_line<0, 128, 4><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 3:  k_line_r<0, 144><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 10: k_line<1, 256, 1><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 11: k_line<1, 128, 3><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 12: k_line<1, 128, 4><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 13: k_line_r<1, 144><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 20: k_line<2, 256, 1><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 21: k_line<2, 128, 3><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        case 22: k_line<2, 128, 4><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-        default: k_line_r<2, 144><<<grid, bs, 0, s>>>(d, k, ja, jw); break;
-    }
+    if (v == 1003) k_line<MODE, 128, 3, NOH><<<grid, bs, 0, s>>>(d, k, ja, jw);
+    else if (v == 1004) k_line<MODE, 128, 4, NOH><<<grid, bs, 0, s>>>(d, k, ja, jw);
+    else if (v == 2007) k_line_r<MODE, 144, NOH><<<grid, bs, 0, s>>>(d, k, ja, jw);
+    else k_line<MODE, 256, 1, NOH><<<grid, bs, 0, s>>>(d, k, ja, jw);
 }
+
+void tc_launch_line_chunk(const TcDev& d, int k, cudaStream_t s, int ja, int jw) {
+    if (d.prec == 1) line_chunk_t<1, false>(d, k, s, ja, jw);
+    else if (d.prec == 2) line_chunk_t<2, false>(d, k, s, ja, jw);
+    else line_chunk_t<0, false>(d, k, s, ja, jw);
+}
+
+void tc_launch_line_chunk_deferred(const TcDev& d, int k, cudaStream_t s, int ja, int jw) {
+    if (d.prec == 1) line_chunk_t<1, true>(d, k, s, ja, jw);
+    else if (d.prec == 2) line_chunk_t<2, true>(d, k, s, ja, jw);
+    else line_chunk_t<0, false>(d, k, s, ja, jw);   // float64: never deferred
+}
+
+void tc_launch_rk_memory(const TcDev& d, int k, cudaStream_t s, int ja, int jw, bool background) {
+    int blocks = (d.Nz * jw + 127) / 128;
+    if (background) {
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+        }
+        blocks = blocks < 4 * sms ? blocks : 4 * sms;
+    }
+    k_rk_memory<<<blocks, 128, 0, s>>>(d, k, ja, jw);
+}
+
+const void* tc_rk_memory_kernel() { return (const void*)k_rk_memory; }
 
 static size_t mean_smem(const TcDev& d) { return (size_t)(2 * d.Nr * 5 * 2 + 2 * d.Nr * 3) * sizeof(double); }
 

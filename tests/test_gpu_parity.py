@@ -92,21 +92,34 @@ def test_one_step_129():
         tc.tc_destroy(h)
 
 
-def test_graph_step_equals_substeps_and_is_deterministic():
+@pytest.mark.parametrize("precision", [tc.TC_PREC_FP64, tc.TC_PREC_MIXED, tc.TC_PREC_DF64])
+def test_graph_step_equals_substeps_and_is_deterministic(precision):
+    """The captured step (in the double-float and mixed forms with the RK
+    memory's implicit part deferred to its own kernel beside the theta rows)
+    equals the substeps launched one by one, bit for bit."""
     v, e = workload_inputs("tc-small-33x16x16")
     cfg = SMALL
     hs = [gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"],
-                   v=v, eta=e) for _ in range(3)]
+                   v=v, eta=e, precision=precision) for _ in range(5)]
     try:
-        tc.tc_step(hs[0], 2)
-        tc.tc_advance_substeps(hs[1], 6)
-        tc.tc_step(hs[2], 2)
-        a, b, c3 = (gpu_state(h, 33, 16, 8) for h in hs)
-        for k in a:
-            assert np.array_equal(a[k], b[k]), k
-            assert np.array_equal(a[k], c3[k]), k
+        tc.tc_step(hs[0], 3)
+        tc.tc_advance_substeps(hs[1], 9)
+        tc.tc_step(hs[2], 3)
+        # the deferred RK memory: three steps in one call (first and next
+        # step graphs), and three calls of one step each
+        tc.tc_set_rk_deferral(hs[3], 1)
+        tc.tc_step(hs[3], 3)
+        tc.tc_set_rk_deferral(hs[4], 1)
+        for _ in range(3):
+            tc.tc_step(hs[4], 1)
+        assert tc.tc_get_rk_deferral(hs[3]) == (precision != tc.TC_PREC_FP64)
+        ref = gpu_state(hs[1], 33, 16, 8)
+        for h in hs[:1] + hs[2:]:
+            g = gpu_state(h, 33, 16, 8)
+            for k in ref:
+                assert np.array_equal(g[k], ref[k]), k
         st = tc.tc_torque_stats(hs[1])
-        assert st["step"] == 2 and abs(st["t"] - 2e-3) < 1e-15
+        assert st["step"] == 3 and abs(st["t"] - 3e-3) < 1e-15
     finally:
         for h in hs:
             tc.tc_destroy(h)
@@ -412,27 +425,32 @@ def test_launch_shapes_change_no_bits(precision):
     cfg = dict(Nr=33, Ntheta=32, Nz=24, zeta=0.883, Re_i=800.0, Re_o=0.0, dt=2e-3)
     v, e = inputs(33, 32, 24, 0.883, 9, "k2", 0.05)
 
-    def run(ztile, variant, chunks):
+    def run(ztile, variant, chunks, rk=0):
         h = gpu_case(cfg["Nr"], cfg["Ntheta"], cfg["Nz"], cfg["zeta"], cfg["Re_i"], cfg["Re_o"], cfg["dt"],
                      v=v, eta=e, precision=precision)
         try:
             tc.tc_set_tiles(h, ztile, variant, chunks)
+            tc.tc_set_rk_deferral(h, rk)
             tc.tc_step(h, 2)
             return gpu_state(h, 33, 24, 16)
         finally:
             tc.tc_destroy(h)
 
     ref = run(8, 128, 1)
-    for zt, lv, ch in [(1, 0, 0), (2, 0, 0), (4, 0, 0)] + [(0, x, 0) for x in tc.LINE_VARIANTS] + \
-            [(1, 0, 2), (1, 0, 4), (1, 0, 8), (2, 0, 8)]:
-        g = run(zt, lv, ch)
+    for zt, lv, ch, rk in [(1, 0, 0, 0), (2, 0, 0, 0), (4, 0, 0, 0)] + [(0, x, 0, 0) for x in tc.LINE_VARIANTS] + \
+            [(1, 0, 2, 0), (1, 0, 4, 0), (1, 0, 8, 0), (2, 0, 8, 0)] + \
+            [(0, 0, 1, 1), (0, 0, 2, 1), (1, 0, 4, 1), (0, 3001, 1, 1), (0, 1004, 2, 1), (0, 0, 0, -1)]:
+        g = run(zt, lv, ch, rk)
         for k in ref:
-            assert np.array_equal(g[k], ref[k]), (zt, lv, ch, k)
+            assert np.array_equal(g[k], ref[k]), (zt, lv, ch, rk, k)
     h = gpu_case(33, 32, 24, 0.883, 800.0, 0.0, 2e-3, precision=precision)
     try:
         for bad in ((3, 0, 0), (0, 100, 0), (16, 0, 0), (0, 0, 3)):
             with pytest.raises(tc.TcError):
                 tc.tc_set_tiles(h, *bad)
+        for bad in (-2, 2):
+            with pytest.raises(tc.TcError):
+                tc.tc_set_rk_deferral(h, bad)
     finally:
         tc.tc_destroy(h)
 
