@@ -734,15 +734,28 @@ void launch_step(tc_handle* h, cudaStream_t s, bool lead, bool trail) {
     const bool defer = defer_rk(h);
     auto pending = [&](int k) { return defer && (k > 0 || lead); };   // an RK memory to add before line k
     if (C <= 1) {
+        // the mean flow (one block) runs beside the line kernel, which does
+        // not touch U, W or the (0,0) slot; the next z inverse waits for it
+        const bool side = h->pipe_ready;
         for (int k = 0; k < 3; ++k) {
+            if (side && k > 0) cudaStreamWaitEvent(s, h->evm, 0);
             tc_launch_plane_kernel(d, 0, s);
             if (pending(k)) rk_fork(h, k > 0 ? k - 1 : 2, s);
             tc_launch_plane_kernel(d, 1, s);
             tc_launch_plane_kernel(d, 2, s);
             if (pending(k)) cudaStreamWaitEvent(s, h->evrk1, 0);
-            line_chunk(h, k, s, 0, d.Nh);
-            tc_launch_mean_phase(d, k, s);
+            if (side) {
+                cudaEventRecord(h->evz[0], s);
+                cudaStreamWaitEvent(h->aux[2], h->evz[0], 0);
+                tc_launch_mean_phase(d, k, h->aux[2]);
+                cudaEventRecord(h->evm, h->aux[2]);
+                line_chunk(h, k, s, 0, d.Nh);
+            } else {
+                line_chunk(h, k, s, 0, d.Nh);
+                tc_launch_mean_phase(d, k, s);
+            }
         }
+        if (side) cudaStreamWaitEvent(s, h->evm, 0);
         if (defer && trail) tc_launch_rk_memory(d, 2, s, 0, d.Nh, false);
         return;
     }

@@ -152,21 +152,23 @@ template <int R, int SIGN, typename T, typename C> __device__ __forceinline__ vo
 // One Stockham butterfly: reads src[j + r M/R], twiddles by
 // exp(SIGN 2 pi i r (j mod Ns)/(Ns R)), R-point DFT, writes
 // dst[(j/Ns) Ns R + (j mod Ns) + r Ns].
+// sh: element stride 2^sh (interleaved columns of the z tiles; 0 for a
+// contiguous column).
 template <int R, int SIGN, typename T, typename C>
-__device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int nb, int Ns, const C* tws) {
+__device__ __forceinline__ void stockham_bfly(const C* sc, C* dcol, int j, int nb, int Ns, const C* tws, int sh = 0) {
     C v[R];
     const int jm = j % Ns;
     #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sc[j + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = sc[(j + r * nb) << sh];
     if (Ns > 1) {
         const C* t = tws + jm * (R - 1);
         #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = c_tw<SIGN>(v[r], t[r - 1]);
     }
     dft<R, SIGN, T>(v);
-    C* dc = dcol + (j / Ns) * Ns * R + jm;
+    C* dc = dcol + (((j / Ns) * Ns * R + jm) << sh);
     #pragma unroll
-    for (int r = 0; r < R; ++r) dc[r * Ns] = v[dft_slot<R>(r)];
+    for (int r = 0; r < R; ++r) dc[(r * Ns) << sh] = v[dft_slot<R>(r)];
 }
 
 // Float64 Stockham butterfly of radix 2, 3 or 4 with the stage twiddles in
@@ -182,23 +184,24 @@ template <int R> __host__ __device__ constexpr int tan_entries() { return R == 2
 // transform whose middle band of outputs is never read.
 template <int R, int SIGN, bool SKIP1 = false>
 __device__ __forceinline__ void stockham_bfly_tan(const double2* sc, double2* dcol, int j, int nb, int Ns,
-                                                  const double* __restrict__ tw) {
+                                                  const double* __restrict__ tw, int sh = 0) {
     static_assert(!SKIP1 || R == 3, "only the radix-3 butterfly skips an output");
     const int jm = j % Ns;
     double2 v[R];
     #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sc[j + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = sc[(j + r * nb) << sh];
     const double* t = tw + jm * tan_entries<R>();
     auto tang = [](double2 a, double tau) {
         const double s = SIGN < 0 ? tau : -tau;
         return make_double2(fma(-s, a.y, a.x), fma(s, a.x, a.y));
     };
-    double2* dc = dcol + (j / Ns) * Ns * R + jm;
+    double2* dc = dcol + (((j / Ns) * Ns * R + jm) << sh);
+    const int o1 = Ns << sh, o2 = (2 * Ns) << sh, o3 = (3 * Ns) << sh;
     if constexpr (R == 2) {
         const double2 u1 = tang(v[1], t[0]);
         const double k1 = t[1];
         dc[0] = make_double2(fma(k1, u1.x, v[0].x), fma(k1, u1.y, v[0].y));
-        dc[Ns] = make_double2(fma(-k1, u1.x, v[0].x), fma(-k1, u1.y, v[0].y));
+        dc[o1] = make_double2(fma(-k1, u1.x, v[0].x), fma(-k1, u1.y, v[0].y));
     } else if constexpr (R == 3) {
         const double2 u1 = tang(v[1], t[0]), u2 = tang(v[2], t[1]);
         const double rho = t[2], k1 = t[3], hk = t[4], sk = SIGN < 0 ? t[5] : -t[5];
@@ -206,8 +209,8 @@ __device__ __forceinline__ void stockham_bfly_tan(const double2* sc, double2* dc
         const double2 bm = make_double2(fma(-rho, u2.x, u1.x), fma(-rho, u2.y, u1.y));
         const double2 t0 = make_double2(fma(-hk, b.x, v[0].x), fma(-hk, b.y, v[0].y));
         dc[0] = make_double2(fma(k1, b.x, v[0].x), fma(k1, b.y, v[0].y));
-        if constexpr (!SKIP1) dc[Ns] = make_double2(fma(sk, bm.y, t0.x), fma(-sk, bm.x, t0.y));
-        dc[2 * Ns] = make_double2(fma(-sk, bm.y, t0.x), fma(sk, bm.x, t0.y));
+        if constexpr (!SKIP1) dc[o1] = make_double2(fma(sk, bm.y, t0.x), fma(-sk, bm.x, t0.y));
+        dc[o2] = make_double2(fma(-sk, bm.y, t0.x), fma(sk, bm.x, t0.y));
     } else {
         const double2 u1 = tang(v[1], t[0]), u2 = tang(v[2], t[1]), u3 = tang(v[3], t[2]);
         const double k1 = t[3], k2 = t[4], rho = t[5];
@@ -217,9 +220,9 @@ __device__ __forceinline__ void stockham_bfly_tan(const double2* sc, double2* dc
         const double2 b = make_double2(fma(rho, u3.x, u1.x), fma(rho, u3.y, u1.y));
         const double2 bm = make_double2(fma(-rho, u3.x, u1.x), fma(-rho, u3.y, u1.y));
         dc[0] = make_double2(fma(k1, b.x, a0.x), fma(k1, b.y, a0.y));
-        dc[2 * Ns] = make_double2(fma(-k1, b.x, a0.x), fma(-k1, b.y, a0.y));
-        dc[Ns] = make_double2(fma(ks, bm.y, a1.x), fma(-ks, bm.x, a1.y));
-        dc[3 * Ns] = make_double2(fma(-ks, bm.y, a1.x), fma(ks, bm.x, a1.y));
+        dc[o2] = make_double2(fma(-k1, b.x, a0.x), fma(-k1, b.y, a0.y));
+        dc[o1] = make_double2(fma(ks, bm.y, a1.x), fma(-ks, bm.x, a1.y));
+        dc[o3] = make_double2(fma(-ks, bm.y, a1.x), fma(ks, bm.x, a1.y));
     }
 }
 
@@ -237,12 +240,12 @@ template <typename C, typename T> __device__ __forceinline__ C c_axpy_r(C acc, T
     return acc;
 }
 template <int R, int SIGN, typename T, typename C>
-__device__ __noinline__ void stockham_bfly_odd(const C* sc, C* dcol, int j, int nb, int Ns, const C* tws) {
+__device__ __noinline__ void stockham_bfly_odd(const C* sc, C* dcol, int j, int nb, int Ns, const C* tws, int sh) {
     constexpr int H = (R - 1) / 2;
     C v[R];
     const int jm = j % Ns;
     #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sc[j + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = sc[(j + r * nb) << sh];
     if (Ns > 1) {
         const C* t = tws + jm * (R - 1);
         #pragma unroll
@@ -257,7 +260,7 @@ __device__ __noinline__ void stockham_bfly_odd(const C* sc, C* dcol, int j, int 
         v[R - q] = b;
         x0 = c_add(x0, a);
     }
-    C* dc = dcol + (j / Ns) * Ns * R + jm;
+    C* dc = dcol + (((j / Ns) * Ns * R + jm) << sh);
     dc[0] = x0;
     #pragma unroll
     for (int k = 1; k <= H; ++k) {
@@ -270,25 +273,28 @@ __device__ __noinline__ void stockham_bfly_odd(const C* sc, C* dcol, int j, int 
             else        s = c_axpy_r(s, -w.y, v[R - q]);
         }
         const C is = c_si<SIGN>(s);
-        dc[k * Ns] = c_add(p, is);
-        dc[(R - k) * Ns] = c_sub(p, is);
+        dc[(k * Ns) << sh] = c_add(p, is);
+        dc[((R - k) * Ns) << sh] = c_sub(p, is);
     }
 }
 template <int SIGN, typename T, typename C>
-__device__ __forceinline__ void stockham_bfly_prime(const C* sc, C* dcol, int j, int nb, int Ns, int R, const C* tws) {
+__device__ __forceinline__ void stockham_bfly_prime(const C* sc, C* dcol, int j, int nb, int Ns, int R, const C* tws,
+                                                    int sh) {
     switch (R) {
-        case 5: stockham_bfly_odd<5, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-        case 7: stockham_bfly_odd<7, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-        case 11: stockham_bfly_odd<11, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-        case 13: stockham_bfly_odd<13, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
-        default: stockham_bfly_odd<17, SIGN, T>(sc, dcol, j, nb, Ns, tws); break;
+        case 5: stockham_bfly_odd<5, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh); break;
+        case 7: stockham_bfly_odd<7, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh); break;
+        case 11: stockham_bfly_odd<11, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh); break;
+        case 13: stockham_bfly_odd<13, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh); break;
+        default: stockham_bfly_odd<17, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh); break;
     }
 }
 
 // ncols transforms of length pl.M stored contiguously in buf0 (column c at
 // c*M), with the plan chosen at run time.  Returns the buffer holding the
 // result (buf0 or buf1).
-template <typename T, int SIGN, int F = 1>
+// IL: the ncols columns are interleaved (element i of column c at
+// i ncols + c, ncols a power of two), else contiguous (column c at c M).
+template <typename T, int SIGN, int F = 1, bool IL = false>
 __device__ typename V2<T>::t* fft_stockham(const TG tg, typename V2<T>::t* buf0, typename V2<T>::t* buf1,
                                            int ncols, const FftPlan& pl,
                                            const typename V2<T>::t* __restrict__ tw) {
@@ -296,28 +302,30 @@ __device__ typename V2<T>::t* fft_stockham(const TG tg, typename V2<T>::t* buf0,
     C* src = buf0;
     C* dst = buf1;
     const int M = pl.M;
+    const int sh = IL ? __ffs(ncols) - 1 : 0;
     for (int s = 0; s < pl.nst; ++s) {
         const int R = pl.R[s], Ns = pl.Ns[s];
         const int nb = M / R;
         const C* tws = tw + pl.twoff[s];
         for (int b = tg.tid; b < ncols * nb; b += tg.nth) {
-            const int col = b / nb;
-            const int j = b - col * nb;
-            const C* sc = src + col * M;
-            C* dcol = dst + col * M;
+            int col, j;
+            if constexpr (IL) { col = b & (ncols - 1); j = b >> sh; }
+            else { col = b / nb; j = b - col * nb; }
+            const C* sc = src + (IL ? col : col * M);
+            C* dcol = dst + (IL ? col : col * M);
             // family 0 plans use radices 2, 3, 4 only: instantiating only
             // those keeps the register demand of the theta kernels low
-            if (R == 3) stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-            else if (R == 4) stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws);
-            else if (R == 2) stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+            if (R == 3) stockham_bfly<3, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh);
+            else if (R == 4) stockham_bfly<4, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh);
+            else if (R == 2) stockham_bfly<2, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh);
             else if (F >= 1 && R == 8) {
-                if constexpr (F >= 1) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+                if constexpr (F >= 1) stockham_bfly<8, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh);
             } else if (F >= 1 && R == 16) {
-                if constexpr (F >= 1) stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws);
+                if constexpr (F >= 1) stockham_bfly<16, SIGN, T>(sc, dcol, j, nb, Ns, tws, sh);
             } else if constexpr (F == 2) {
                 // odd prime stages: only in the kernels instantiated for axial
                 // lengths with factors 5..17 (their register demand is higher)
-                stockham_bfly_prime<SIGN, T>(sc, dcol, j, nb, Ns, R, tws);
+                stockham_bfly_prime<SIGN, T>(sc, dcol, j, nb, Ns, R, tws, sh);
             }
         }
         __syncthreads();
@@ -380,19 +388,19 @@ __host__ __device__ constexpr int plan_tan_off(int M, int s, int F = 0) {
 // zero band for every j < M/3, so the butterfly skips it.  With v1 = 0 the
 // radix-3 sums are bit for bit those of the full butterfly.
 template <int SIGN, typename T, typename C>
-__device__ __forceinline__ void stockham_bfly3_zero_mid(const C* sc, C* dcol, int j, int nb) {
+__device__ __forceinline__ void stockham_bfly3_zero_mid(const C* sc, C* dcol, int j, int nb, int sh = 0) {
     const T h = (T)0.5;
     const T s3 = (T)0.86602540378443864676;   // sin(2 pi/3)
-    const C v0 = sc[j], v2 = sc[j + 2 * nb];
+    const C v0 = sc[j << sh], v2 = sc[(j + 2 * nb) << sh];
     C t0; t0.x = v0.x - h * v2.x; t0.y = v0.y - h * v2.y;
     C id = c_si<SIGN>(v2); id.x *= s3; id.y *= s3;   // SIGN i s3 v2 = -(SIGN i s3 (0 - v2))
-    C* dc = dcol + 3 * j;
+    C* dc = dcol + ((3 * j) << sh);
     dc[0] = c_add(v0, v2);
-    dc[1] = c_sub(t0, id);
-    dc[2] = c_add(t0, id);
+    dc[1 << sh] = c_sub(t0, id);
+    dc[2 << sh] = c_add(t0, id);
 }
 
-template <typename T, int SIGN, int M, int F, int S, bool Z0 = false>
+template <typename T, int SIGN, int M, int F, int S, bool Z0 = false, bool IL = false>
 __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(const TG tg, typename V2<T>::t* src, typename V2<T>::t* dst,
                                                               int ncols, const typename V2<T>::t* __restrict__ tw,
                                                               const double* __restrict__ twtan) {
@@ -405,20 +413,24 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(const TG tg, typen
         constexpr int Ns = plan_ns_f(M, S, F);
         constexpr int nb = M / R;
         const C* tws = tw + plan_off_f(M, S, F);
+        const int sh = IL ? __ffs(ncols) - 1 : 0;
         for (int b = tg.tid; b < ncols * nb; b += tg.nth) {
-            const int col = b / nb;
-            const int j = b - col * nb;
+            int col, j;
+            if constexpr (IL) { col = b & (ncols - 1); j = b >> sh; }
+            else { col = b / nb; j = b - col * nb; }
+            const C* sc = src + (IL ? col : col * M);
+            C* dc = dst + (IL ? col : col * M);
             if constexpr (Z0 && S == 0 && R == 3)
-                stockham_bfly3_zero_mid<SIGN, T>(src + col * M, dst + col * M, j, nb);
+                stockham_bfly3_zero_mid<SIGN, T>(sc, dc, j, nb, sh);
             else if constexpr (F == 3 && S + 1 == plan_nst_f(M, F))   // last stage, radix 3: skip band 1
-                stockham_bfly_tan<R, SIGN, true>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S, F));
+                stockham_bfly_tan<R, SIGN, true>(sc, dc, j, nb, Ns, twtan + plan_tan_off(M, S, F), sh);
             else if constexpr (std::is_same<T, double>::value && (F == 0 || F == 3) && Ns > 1)
-                stockham_bfly_tan<R, SIGN>(src + col * M, dst + col * M, j, nb, Ns, twtan + plan_tan_off(M, S, F));
+                stockham_bfly_tan<R, SIGN>(sc, dc, j, nb, Ns, twtan + plan_tan_off(M, S, F), sh);
             else
-                stockham_bfly<R, SIGN, T>(src + col * M, dst + col * M, j, nb, Ns, tws);
+                stockham_bfly<R, SIGN, T>(sc, dc, j, nb, Ns, tws, sh);
         }
         __syncthreads();
-        return fft_fixed_stage<T, SIGN, M, F, S + 1, Z0>(tg, dst, src, ncols, tw, twtan);
+        return fft_fixed_stage<T, SIGN, M, F, S + 1, Z0, IL>(tg, dst, src, ncols, tw, twtan);
     }
 }
 
@@ -430,19 +442,19 @@ __device__ __forceinline__ typename V2<T>::t* fft_fixed_stage(const TG tg, typen
 // first stage of the compile-time plans skips.  Families 0 and 3 of the
 // float64 z transforms are launched only for lengths with a compile-time
 // plan (the host checks tc_fft_fixed_length).
-template <typename T, int SIGN, int F, bool Z0 = false>
+template <typename T, int SIGN, int F, bool Z0 = false, bool IL = false>
 __device__ typename V2<T>::t* fft(const TG tg, typename V2<T>::t* buf0, typename V2<T>::t* buf1, int ncols,
                                   const FftPlan& pl, const typename V2<T>::t* __restrict__ tw,
                                   const double* __restrict__ twtan = nullptr) {
-#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0, Z0>(tg, buf0, buf1, ncols, tw, twtan);
+#define TC_FFT_CASE(MM) case MM: return fft_fixed_stage<T, SIGN, MM, F, 0, Z0, IL>(tg, buf0, buf1, ncols, tw, twtan);
     if constexpr (F == 2) {
-        return fft_stockham<T, SIGN, 2>(tg, buf0, buf1, ncols, pl, tw);
+        return fft_stockham<T, SIGN, 2, IL>(tg, buf0, buf1, ncols, pl, tw);
     } else {
         switch (pl.M) {
             TC_FFT_CASE(12) TC_FFT_CASE(18) TC_FFT_CASE(24) TC_FFT_CASE(36) TC_FFT_CASE(48)
             TC_FFT_CASE(72) TC_FFT_CASE(96) TC_FFT_CASE(144) TC_FFT_CASE(192) TC_FFT_CASE(288)
             TC_FFT_CASE(384) TC_FFT_CASE(576) TC_FFT_CASE(768) TC_FFT_CASE(1152) TC_FFT_CASE(1536)
-            default: return fft_stockham<T, SIGN, (F == 3 ? 0 : F)>(tg, buf0, buf1, ncols, pl, tw);
+            default: return fft_stockham<T, SIGN, (F == 3 ? 0 : F), IL>(tg, buf0, buf1, ncols, pl, tw);
         }
     }
 #undef TC_FFT_CASE
@@ -572,6 +584,9 @@ __device__ __forceinline__ void zinv_body(const TcDev& d, const double2* __restr
     const int j0 = (bx + tile0) * ct;
     const double2* src = f == 0 ? f0 : (f == 1 ? f1 : f2);
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh;
+    // the ct columns interleaved in shared memory (element q of column c at
+    // q ct + c = idx): the global rows and the shared tile are both read and
+    // written in order, without bank conflicts
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx >> lct, c = idx & (ct - 1);
         int s = -1;
@@ -582,14 +597,15 @@ __device__ __forceinline__ void zinv_body(const TcDev& d, const double2* __restr
             double2 x = src[((size_t)r * Nz + s) * Nh + j0 + c];
             val.x = from_f64<T>(x.x); val.y = from_f64<T>(x.y);
         }
-        buf0[c * Mz + q] = val;
+        buf0[idx] = val;
     }
     __syncthreads();
-    C* res = fft<T, +1, ZF, (ZF == 0)>(tg_block(), buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d), d.twz_tan);
+    C* res = fft<T, +1, ZF, (ZF == 0), true>(tg_block(), buf0, buf1, ct, ZF == 0 ? d.pz0 : d.pz, twz_of<T, ZF>(d),
+                                             d.twz_tan);
     C* out = reinterpret_cast<C*>(d.zbuf) + ((size_t)f * d.Nr + r) * Mz * Nh;
     for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
         const int q = idx >> lct, c = idx & (ct - 1);
-        out[(size_t)q * Nh + j0 + c] = res[c * Mz + q];
+        out[(size_t)q * Nh + j0 + c] = res[idx];
     }
 }
 template <typename T, int ZF>
@@ -929,15 +945,15 @@ __device__ __forceinline__ void zfwd_body(const TcDev& d, int tile0, int bx, int
     const int j0 = (bx + tile0) * ct;
     const int Mz = d.Mz, Nz = d.Nz, Nh = d.Nh, Nr = d.Nr;
     const C* in = reinterpret_cast<const C*>(d.pbuf) + ((size_t)p * Nr + r) * Mz * Nh;
-    for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < ct * Mz; idx += blockDim.x) {     // interleaved columns, as in zinv_body
         const int q = idx >> lct, c = idx & (ct - 1);
-        buf0[c * Mz + q] = in[(size_t)q * Nh + j0 + c];
+        buf0[idx] = in[(size_t)q * Nh + j0 + c];
     }
     __syncthreads();
     // family 3 (float64): the last stage skips outputs M/3 .. 2M/3 - 1, i.e.
     // q = Nz/2 .. Nz - 1, which the truncation below never reads
-    C* res = fft<T, -1, ZF>(tg_block(), buf0, buf1, ct, (ZF == 0 || ZF == 3) ? d.pz0 : d.pz, twz_of<T, ZF>(d),
-                            ZF == 3 ? d.twz3_tan : d.twz_tan);
+    C* res = fft<T, -1, ZF, false, true>(tg_block(), buf0, buf1, ct, (ZF == 0 || ZF == 3) ? d.pz0 : d.pz,
+                                         twz_of<T, ZF>(d), ZF == 3 ? d.twz3_tan : d.twz_tan);
     T scale;
     if constexpr (std::is_same<T, double>::value) scale = 1.0;     // applied in k_rows
     else if constexpr (std::is_same<T, float>::value) scale = d.fscale_f;
@@ -952,7 +968,7 @@ __device__ __forceinline__ void zfwd_body(const TcDev& d, int tile0, int bx, int
         if (s != Nz / 2) {
             const int n = s < Nz / 2 ? s : s - Nz;
             const int qq = n >= 0 ? n : Mz + n;
-            val = res[c * Mz + qq];
+            val = res[(qq << lct) + c];
             if constexpr (!std::is_same<T, double>::value) { val.x *= scale; val.y *= scale; }
         }
         outp[(size_t)s * Nh + j0 + c] = val;
