@@ -74,6 +74,9 @@ __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 // registers in a kernel that is already at its register budget)
 __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(d_bits(a.x), d_bits(a.y)); }
 __device__ __forceinline__ double2 to_d2(dcomplex a) { return make_double2((double)a.x, (double)a.y); }
+// the same exact widening by bit operations and one float64 add (d_of), for
+// the mixed form's continuity term
+__device__ __forceinline__ double2 to_d2_bits(dcomplex a) { return make_double2(d_of(a.x), d_of(a.y)); }
 template <typename CT> __device__ __forceinline__ CT from_d2(double2 a);
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2(f_bits(a.x), f_bits(a.y)); }
@@ -527,7 +530,7 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
             // double-float, then widened to float64
             dcomplex cc;
             for (int s = 0; s < 5; ++s) cc = dc_fma(cc, l2x[j * 5 + s], Cp[s]);
-            r = to_d2(dc_fma(dc_of(acc), m3nu, cc));
+            r = to_d2_bits(dc_fma(dc_of(acc), m3nu, cc));
         } else {
             r = to_d2(acc);
         }
