@@ -63,6 +63,8 @@ def parse():
                    help="pin the line-kernel variant (0: chosen by timing; the launch shape changes no bits)")
     p.add_argument("--ztile", type=int, default=0,
                    help="pin the z tile of the z kernels (0: chosen by timing)")
+    p.add_argument("--rk-deferral", type=int, default=-1, choices=[-1, 0, 1],
+                   help="pin the deferred RK memory of the df64 and mixed forms (-1: chosen by timing)")
     return p.parse_args()
 
 
@@ -347,6 +349,8 @@ def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False,
     W0 = tc.tc_get_field(h, tc.TC_FIELD_MEAN_W)
     if args.column_groups or args.line_variant or args.ztile:
         tc.tc_set_tiles(h, args.ztile, args.line_variant, args.column_groups)
+    if args.rk_deferral >= 0:
+        tc.tc_set_rk_deferral(h, args.rk_deferral)
     # warm-up steps (the first call of five or more steps also runs the
     # autotuner's timed choice of column groups and RK-memory deferral)
     tc.tc_step(h, warmup_steps(args))
