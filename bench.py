@@ -413,7 +413,7 @@ def torque_summary(series):
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel on the paper workload 129 x 512 x 170, 32895 rows per launch; the
 # per-row traffic does not depend on Nr or Nz.
-ROWS_FP64_BYTES_PER_ROW = {512: (404588032 + 622788864) / 32895}
+ROWS_FP64_BYTES_PER_ROW = {512: (404781824 + 630402816) / 32895}
 ROWS_FP64_CAPTURE_CURRENT = True
 
 
