@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     p.add_argument("--workload", default="tc-257x512x512")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other precision forms")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -333,6 +333,81 @@ def warmup_steps(args):
     return max(args.warmup, 5)
 
 
+def e2e_pipelined(args, tc, torch, h, v, e, gp, world, dist, local):
+    """The metric end to end through the public API with host buffers.  Every
+    step: the state v, eta in from page-locked host memory, one step, v, eta
+    out to page-locked host memory, and the torque statistics.  The copies are
+    pipelined as a data loader does: while step i runs, the input of step
+    i + 1 crosses the host link into a device staging buffer (its own
+    stream) and the result of step i - 1 crosses back from another; before
+    the step, tc_set_field_async loads the staged input into the state
+    (device to device), and after it tc_get_field_async copies the state
+    into the outgoing staging buffer.  Setting the state restarts the RK
+    memory, so each step also runs k_init."""
+    import numpy as np
+    nb = tc.tc_field_bytes(h, tc.TC_FIELD_V)
+    n8 = nb // 8
+    stream = torch.cuda.current_stream()            # the handle's launch stream
+    pin = {k: torch.empty(n8, dtype=torch.float64, pin_memory=True) for k in ("vi", "ei", "vo", "eo")}
+    pin["vi"].numpy().view(np.complex128)[:] = v.ravel()
+    pin["ei"].numpy().view(np.complex128)[:] = e.ravel()
+    pin["vo"].zero_()
+    pin["eo"].zero_()
+    stage = {k: torch.empty(n8, dtype=torch.float64, device=f"cuda:{local}") for k in ("vi", "ei", "vo", "eo")}
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {k: torch.cuda.Event() for k in ("in_ready", "in_free", "out_ready", "out_free")}
+    torch.cuda.synchronize()
+
+    def upload():                                   # host -> staging, once the last input was loaded
+        s_in.wait_event(ev["in_free"])
+        with torch.cuda.stream(s_in):
+            stage["vi"].copy_(pin["vi"], non_blocking=True)
+            stage["ei"].copy_(pin["ei"], non_blocking=True)
+        ev["in_ready"].record(s_in)
+
+    def download():                                 # staging -> host, during the next step
+        s_out.wait_event(ev["out_ready"])
+        with torch.cuda.stream(s_out):
+            pin["vo"].copy_(stage["vo"], non_blocking=True)
+            pin["eo"].copy_(stage["eo"], non_blocking=True)
+        ev["out_free"].record(s_out)
+
+    def run(k):
+        ev["in_free"].record(stream)
+        ev["out_free"].record(stream)
+        upload()
+        stats = None
+        for i in range(k):
+            stream.wait_event(ev["in_ready"])
+            tc.tc_set_field_async(h, tc.TC_FIELD_V, stage["vi"].data_ptr(), nb)
+            tc.tc_set_field_async(h, tc.TC_FIELD_ETA, stage["ei"].data_ptr(), nb)
+            ev["in_free"].record(stream)
+            if i + 1 < k:
+                upload()                            # the next step's input, during this step
+            tc.tc_step(h, 1)
+            stream.wait_event(ev["out_free"])
+            tc.tc_get_field_async(h, tc.TC_FIELD_V, stage["vo"].data_ptr(), nb)
+            tc.tc_get_field_async(h, tc.TC_FIELD_ETA, stage["eo"].data_ptr(), nb)
+            ev["out_ready"].record(stream)
+            download()                              # this step's result, during the next step
+            stats = tc.tc_torque_stats(h)
+        s_out.synchronize()
+        return stats
+
+    run(1)                                          # untimed warm-up of the pipeline
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = run(args.e2e_steps)
+    wall = dist.max(time.perf_counter() - t0)
+    ok = bool(np.isfinite(pin["vo"].numpy()).all()) and float(np.abs(pin["vo"].numpy()).max()) > 0
+    return {"value": gp * args.e2e_steps * world / wall, "unit": UNIT,
+            "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + ctypes.sizeof(tc.tc_stats),
+            "steps": args.e2e_steps, "torque_inner": stats["G_inner"], "ms_per_step": 1e3 * wall / args.e2e_steps,
+            "pipelined": "host copies of step i+1's input and step i-1's result overlap step i (device staging buffers)",
+            "result_read_back": ok}
+
+
 def time_form(tc, torch, w, prec, v, e, args, local, dist, measure_clocks=False, torque_steps=0):
     """Create the case in one precision form, warm up, time K steps with CUDA
     events on the launch stream, then time each kernel (tc_phase_times).
@@ -496,43 +571,7 @@ def run_gpu(args):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        nb = tc.tc_field_bytes(h, tc.TC_FIELD_V)
-        pin = {k: torch.empty(nb // 8, dtype=torch.float64, pin_memory=True) for k in ("vi", "ei", "vo", "eo")}
-        pin["vi"].numpy().view(np.complex128)[:] = v.ravel()
-        pin["ei"].numpy().view(np.complex128)[:] = e.ravel()
-        pin["vo"].zero_()
-        pin["eo"].zero_()
-        torch.cuda.synchronize()
-        # per step: the state in from page-locked host memory (queued on the
-        # launch stream ahead of the step), the step, then the state out on a
-        # second stream while the torque statistics run on the first
-        side = torch.cuda.Stream()
-        part = {"h2d_enqueue": 0.0, "h2d_and_step": 0.0, "d2h_enqueue": 0.0, "stats_and_d2h": 0.0}
-        t0 = time.perf_counter()
-        for it in range(-1, args.e2e_steps):      # iteration -1: untimed warm-up
-            if it == 0:
-                t0 = time.perf_counter()
-                part = dict.fromkeys(part, 0.0)
-            ta = time.perf_counter()
-            tc.tc_set_field_async(h, tc.TC_FIELD_V, pin["vi"].data_ptr(), nb)
-            tc.tc_set_field_async(h, tc.TC_FIELD_ETA, pin["ei"].data_ptr(), nb)
-            tb = time.perf_counter()
-            tc.tc_step(h, 1)
-            tcs = time.perf_counter()
-            tc.tc_get_field_async(h, tc.TC_FIELD_V, pin["vo"].data_ptr(), nb, side.cuda_stream)
-            tc.tc_get_field_async(h, tc.TC_FIELD_ETA, pin["eo"].data_ptr(), nb, side.cuda_stream)
-            td = time.perf_counter()
-            stats = tc.tc_torque_stats(h)
-            side.synchronize()
-            te = time.perf_counter()
-            for k, dt_ in (("h2d_enqueue", tb - ta), ("h2d_and_step", tcs - tb), ("d2h_enqueue", td - tcs),
-                           ("stats_and_d2h", te - td)):
-                part[k] += 1e3 * dt_ / args.e2e_steps
-        wall = dist.max(time.perf_counter() - t0)
-        e2e = {"value": gp * args.e2e_steps * world / wall, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": 2 * nb + ctypes.sizeof(tc.tc_stats),
-               "steps": args.e2e_steps, "torque_inner": stats["G_inner"],
-               "ms_per_step_by_call": {k: round(x, 2) for k, x in part.items()}}
+        e2e = e2e_pipelined(args, tc, torch, h, v, e, gp, world, dist, local)
     device_bytes = tc.tc_device_bytes(h)
     shapes = main["launch_shapes"]
     tc.tc_destroy(h)

@@ -156,16 +156,20 @@ int tc_get_field(tc_handle* h, int which, int space, void* host_buf, size_t byte
 int tc_set_field(tc_handle* h, int which, const void* host_buf, size_t bytes);
 
 /* The same without waiting (spectral space and mean profiles only), for
- * callers that overlap their copies with other work; host_buf must stay
- * valid, and should be page-locked, until the copy has run.
+ * callers that overlap their copies with other work; buf must stay valid,
+ * and host memory should be page-locked, until the copy has run.  buf may
+ * also be device memory of the handle's GPU (the copy direction follows
+ * from the address): a caller that moves the next input from the host into
+ * a device staging buffer while a step runs, and reads results back through
+ * one, overlaps the host link with the steps.
  *   tc_set_field_async: queued on the handle's stream (so ordered before the
  *     next step, which also runs there); the RK memory restarts as above.
  *   tc_get_field_async: the copy is ordered after everything queued so far on
  *     the handle's stream and runs on `cuda_stream` (NULL: the handle's
- *     stream); the caller waits for that stream before reading host_buf.
- * A pageable host_buf makes the copy synchronous. */
-int tc_set_field_async(tc_handle* h, int which, const void* host_buf, size_t bytes);
-int tc_get_field_async(tc_handle* h, int which, void* host_buf, size_t bytes, void* cuda_stream);
+ *     stream); the caller waits for that stream before reading buf.
+ * A pageable host buffer makes the copy synchronous. */
+int tc_set_field_async(tc_handle* h, int which, const void* buf, size_t bytes);
+int tc_get_field_async(tc_handle* h, int which, void* buf, size_t bytes, void* cuda_stream);
 
 /* Bytes of one field in the given space. */
 size_t tc_field_bytes(const tc_handle* h, int which, int space);

@@ -366,16 +366,17 @@ def tc_estimate_device_bytes(params):
     return lib().tc_estimate_device_bytes(ctypes.byref(params))
 
 
-def tc_set_field_async(h, which, host_ptr, nbytes):
-    """tc_set_field from a caller-owned (page-locked) host address, without
-    waiting."""
-    return _check(lib().tc_set_field_async(h, which, host_ptr, nbytes))
+def tc_set_field_async(h, which, ptr, nbytes):
+    """tc_set_field from a caller-owned address, without waiting: page-locked
+    host memory, or device memory of the handle's GPU."""
+    return _check(lib().tc_set_field_async(h, which, ptr, nbytes))
 
 
-def tc_get_field_async(h, which, host_ptr, nbytes, stream_ptr=None):
-    """Spectral field into a caller-owned host address, ordered after the
-    handle's queued work and run on stream_ptr (None: the handle's stream)."""
-    return _check(lib().tc_get_field_async(h, which, host_ptr, nbytes, stream_ptr))
+def tc_get_field_async(h, which, ptr, nbytes, stream_ptr=None):
+    """Spectral field into a caller-owned address (page-locked host memory, or
+    device memory of the handle's GPU), ordered after the handle's queued
+    work and run on stream_ptr (None: the handle's stream)."""
+    return _check(lib().tc_get_field_async(h, which, ptr, nbytes, stream_ptr))
 
 
 def tc_split_set(h, r0, r1, j0, j1):

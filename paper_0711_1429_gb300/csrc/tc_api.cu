@@ -1325,7 +1325,7 @@ static int set_field_impl(tc_handle* h, int which, const void* buf, size_t bytes
     TcDev& d = h->d;
     if (which == TC_FIELD_MEAN_U || which == TC_FIELD_MEAN_W) {
         if (bytes != (size_t)d.Nr * sizeof(double)) { set_err("mean profile needs Nr float64"); return TC_ERR_SIZE; }
-        CK(cudaMemcpyAsync(which == TC_FIELD_MEAN_U ? d.U : d.W, buf, bytes, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(which == TC_FIELD_MEAN_U ? d.U : d.W, buf, bytes, cudaMemcpyDefault, h->stream));
         if (sync) CK(cudaStreamSynchronize(h->stream));
         h->need_init = true;
         h->phase = 0;
@@ -1335,7 +1335,7 @@ static int set_field_impl(tc_handle* h, int which, const void* buf, size_t bytes
     const size_t need = (size_t)d.Nr * d.npairs * sizeof(double2);
     if (bytes != need) { set_err("buffer size " + std::to_string(bytes) + " != " + std::to_string(need)); return TC_ERR_SIZE; }
     double2* dst = which == TC_FIELD_V ? d.v : d.eta;
-    CK(cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyDefault, h->stream));   // host or device source
     // Hermitian m = 0 column, zero Nyquist slot and (0,0), on the device
     tc_launch_realify(d, dst, h->stream);
     CK(cudaGetLastError());
@@ -1377,7 +1377,7 @@ int tc_get_field_async(tc_handle* h, int which, void* buf, size_t bytes, void* s
         cudaEventDestroy(ev);
         CK(e);
     }
-    CK(cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDefault, s));   // host or device destination
     return TC_OK;
 }
 

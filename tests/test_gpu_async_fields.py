@@ -41,3 +41,34 @@ def test_async_copies_equal_the_waiting_ones():
     finally:
         tc.tc_destroy(ref)
         tc.tc_destroy(h)
+
+
+def test_async_copies_through_device_staging_buffers():
+    """The same with device buffers on both sides: the input staged on the
+    device (as a pipelined caller does) and the result read into device
+    memory, then checked on the host."""
+    torch = pytest.importorskip("torch")
+    ensure_lib()
+    Nr, Nt, Nz = 33, 32, 32
+    v, e = inputs(Nr, Nt, Nz, 0.883, 8, "k2", 0.05)
+    ref = gpu_case(Nr, Nt, Nz, 0.883, 1000.0, 0.0, 1e-3, v=v, eta=e)
+    h = gpu_case(Nr, Nt, Nz, 0.883, 1000.0, 0.0, 1e-3)
+    try:
+        tc.tc_step(ref, 2)
+        nb = tc.tc_field_bytes(h, tc.TC_FIELD_V)
+        dev = {k: torch.empty(nb // 8, dtype=torch.float64, device="cuda") for k in ("vi", "ei", "vo", "eo")}
+        dev["vi"].copy_(torch.from_numpy(v.ravel().view(np.float64)))
+        dev["ei"].copy_(torch.from_numpy(e.ravel().view(np.float64)))
+        torch.cuda.synchronize()
+        tc.tc_set_stream(h, torch.cuda.current_stream().cuda_stream)
+        tc.tc_set_field_async(h, tc.TC_FIELD_V, dev["vi"].data_ptr(), nb)
+        tc.tc_set_field_async(h, tc.TC_FIELD_ETA, dev["ei"].data_ptr(), nb)
+        tc.tc_step(h, 2)
+        tc.tc_get_field_async(h, tc.TC_FIELD_V, dev["vo"].data_ptr(), nb)
+        tc.tc_get_field_async(h, tc.TC_FIELD_ETA, dev["eo"].data_ptr(), nb)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev["vo"].cpu().numpy().view(np.complex128), tc.tc_get_field(ref, tc.TC_FIELD_V))
+        assert np.array_equal(dev["eo"].cpu().numpy().view(np.complex128), tc.tc_get_field(ref, tc.TC_FIELD_ETA))
+    finally:
+        tc.tc_destroy(ref)
+        tc.tc_destroy(h)
