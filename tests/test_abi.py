@@ -49,6 +49,10 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.tc_state_bytes(None) == 0
     assert lib.tc_save_state(None, None, 0) == tc.TC_ERR_ARG
     assert lib.tc_load_state(None, None, 0) == tc.TC_ERR_ARG
+    assert lib.tc_set_rk_deferral(None, 1) == tc.TC_ERR_ARG
+    assert lib.tc_get_rk_deferral(None, None) == tc.TC_ERR_ARG
+    assert lib.tc_set_field_async(None, 0, None, 0) == tc.TC_ERR_ARG
+    assert lib.tc_get_field_async(None, 0, None, 0, None) == tc.TC_ERR_ARG
     lib.tc_destroy(None)
 
 
