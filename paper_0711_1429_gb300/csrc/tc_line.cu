@@ -462,6 +462,12 @@ __device__ __forceinline__ void rk_memory_row(const TcDev& d, int pair, int jr, 
 // each field is the same in every role.  With NOH the implicit part of the
 // next RK memory is left to k_rk_memory (launched after this kernel, before
 // the next substep's line kernel).
+// Roles 1 and 2 run in two warps of one block and keep step: the eta thread
+// reads v of the old state at row i while the v thread overwrites row i - 2
+// with its elimination, so a block barrier opens every iteration of the
+// forward sweep and closes the sweep.  Every thread of such a block runs the
+// same loop: a thread without a pair works on a stand-in pair (n = 0,
+// j = 1, always evolved) and stores nothing.
 template <int MODE, int ROLE, bool NOH = false>
 __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int jw, const int idx, int& pair_out,
                                             double& m_out, double& al_out, long long& partner_out) {
@@ -469,12 +475,19 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
     constexpr bool DV = ROLE != 2, DE = ROLE != 1;
     typedef typename LineTypes<MODE>::T T;
     typedef typename LineTypes<MODE>::CT CT;
+    constexpr bool SYNC = ROLE != 0;
     // thread idx -> pair among the columns ja .. ja + jw - 1 of every axial slot
-    if (idx >= d.Nz * jw) return false;
-    const int pair = (idx / jw) * d.Nh + ja + idx % jw;
-    double m, al;
-    long long partner;
-    if (!pair_info(d, pair, m, al, partner)) return false;
+    bool act = idx < d.Nz * jw;
+    int pair = act ? (idx / jw) * d.Nh + ja + idx % jw : 0;
+    double m = 0.0, al = 0.0;
+    long long partner = -1;
+    if (act) act = pair_info(d, pair, m, al, partner);
+    if (!act) {
+        if constexpr (!SYNC) return false;
+        pair = 1;                                   // stand-in: loads only
+        pair_info(d, pair, m, al, partner);
+        partner = -1;
+    }
     pair_out = pair; m_out = m; al_out = al; partner_out = partner;
     const int N = d.Nr;
     const size_t P = d.npairs;
@@ -540,29 +553,30 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
     auto rhs_v = [&](int j, double2 E) -> double2 {
         const size_t o = (size_t)j * P + pair;
         const double2 r = caxpy(d.Hv[o], gdt, E);
-        d.Hv[o] = caxpy(r, zdt, E);
+        if (act) d.Hv[o] = caxpy(r, zdt, E);
         return r;
     };
     auto rhs_e = [&](int j, double2 E) -> double2 {
         const size_t o = (size_t)j * P + pair;
         const double2 r = caxpy(d.He[o], gdt, E);
-        d.He[o] = caxpy(r, zdt, E);
+        if (act) d.He[o] = caxpy(r, zdt, E);
         return r;
     };
     auto fwd_v = [&](int j, double2 r) {
         const double m2 = TAB(d.tab_luv, k, j, 0), m1 = TAB(d.tab_luv, k, j, 1);
         const double2 y = caxpy(caxpy(r, -m2, yv2), -m1, yv1);
-        d.v[(size_t)j * P + pair] = y;
+        if (act) d.v[(size_t)j * P + pair] = y;
         yv2 = yv1; yv1 = y;
     };
     auto fwd_e = [&](int j, double2 r) {
         const double m2 = TAB(d.tab_lue, k, j, 0), m1 = TAB(d.tab_lue, k, j, 1);
         const double2 y = caxpy(caxpy(r, -m2, ye2), -m1, ye1);
-        d.eta[(size_t)j * P + pair] = y;
+        if (act) d.eta[(size_t)j * P + pair] = y;
         ye2 = ye1; ye1 = y;
     };
 
     for (int i = 0; i < N; ++i) {
+        if constexpr (SYNC) __syncthreads();    // the two roles within one row of each other
         for (int s = 0; s < 4; ++s) {
             if constexpr (DV) { Av[s] = Av[s + 1]; Bv[s] = Bv[s + 1]; Cv[s] = Cv[s + 1]; Cp[s] = Cp[s + 1]; }
             if constexpr (DE) { Ae[s] = Ae[s + 1]; Be[s] = Be[s + 1]; }
@@ -632,17 +646,20 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
         }
     }
 
+    if constexpr (SYNC) __syncthreads();        // the forward reads of both roles are done
     // ---- backward sweep: back substitution, H_(k+1) += (beta+alpha') dt L x ----
     double2 xw[5], ew[5];
     double k2w[5];
     for (int s = 0; s < 5; ++s) { xw[s] = cz(); ew[s] = cz(); k2w[s] = 0.0; }
     bool bad = false;
     if constexpr (!NOH) k2w[0] = k2_at(m, al, d.rinv[N - 1]);
-    if constexpr (DV) d.v[(size_t)(N - 1) * P + pair] = cz();
-    if constexpr (DE) d.eta[(size_t)(N - 1) * P + pair] = cz();
+    if (act) {
+        if constexpr (DV) d.v[(size_t)(N - 1) * P + pair] = cz();
+        if constexpr (DE) d.eta[(size_t)(N - 1) * P + pair] = cz();
+    }
     const double hdtnu = hdt * nu;
     auto h_update = [&](int jr, bool do_v, bool do_e) {
-        if constexpr (!NOH) rk_memory_row(d, pair, jr, xw, ew, k2w, hdt, hdtnu, do_v && DV, do_e && DE);
+        if constexpr (!NOH) rk_memory_row(d, pair, jr, xw, ew, k2w, hdt, hdtnu, do_v && DV && act, do_e && DE && act);
     };
     for (int i = N - 2; i >= 0; --i) {
         for (int s = 4; s > 0; --s) { xw[s] = xw[s - 1]; ew[s] = ew[s - 1]; k2w[s] = k2w[s - 1]; }
@@ -655,8 +672,10 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
                                           caxpy(caxpy(yv, -TAB(d.tab_luv, k, i, 3), xw[1]), -TAB(d.tab_luv, k, i, 4), xw[2]));
                 bad |= !cfinite(xv);
                 xw[0] = xv;
-                d.v[o] = xv;
-                if (partner >= 0) d.v[(size_t)i * P + partner] = cconj(xv);
+                if (act) {
+                    d.v[o] = xv;
+                    if (partner >= 0) d.v[(size_t)i * P + partner] = cconj(xv);
+                }
             }
             if constexpr (DE) {
                 const double2 ye = d.eta[o];
@@ -664,25 +683,29 @@ __device__ __forceinline__ bool line_sweeps(const TcDev& d, int k, int ja, int j
                                           caxpy(caxpy(ye, -TAB(d.tab_lue, k, i, 3), ew[1]), -TAB(d.tab_lue, k, i, 4), ew[2]));
                 bad |= !cfinite(xe);
                 ew[0] = xe;
-                d.eta[o] = xe;
-                if (partner >= 0) d.eta[(size_t)i * P + partner] = cconj(xe);
+                if (act) {
+                    d.eta[o] = xe;
+                    if (partner >= 0) d.eta[(size_t)i * P + partner] = cconj(xe);
+                }
             }
         } else {
             xw[0] = cz(); ew[0] = cz();
-            if constexpr (DV) d.v[pair] = cz();
-            if constexpr (DE) d.eta[pair] = cz();
+            if (act) {
+                if constexpr (DV) d.v[pair] = cz();
+                if constexpr (DE) d.eta[pair] = cz();
+            }
         }
         if (i == N - 5) h_update(N - 2, false, true);          // one-sided eta row N-2
         const int jr = i + 2;
         if (i <= N - 5 && jr >= 2) h_update(jr, true, true);
         if (i == 0) h_update(1, false, true);                  // one-sided eta row 1
     }
-    if (bad) atomicOr(d.flag, 1);
-    if (partner >= 0) {
+    if (bad && act) atomicOr(d.flag, 1);
+    if (act && partner >= 0) {
         if constexpr (DV) { d.v[(size_t)(N - 1) * P + partner] = cz(); d.v[partner] = cz(); }
         if constexpr (DE) { d.eta[(size_t)(N - 1) * P + partner] = cz(); d.eta[partner] = cz(); }
     }
-    return true;
+    return act;
 }
 
 template <int MODE, bool NOH = false>
